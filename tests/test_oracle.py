@@ -1,0 +1,296 @@
+"""Pins for the CPU oracle (no GPU): hand-enumerated rounds, closed forms,
+invariants and brute force.  Each test names the passage it pins."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _log(rows):
+    a = np.zeros(len(rows), wl.LOG_DTYPE)
+    for i, (addr, val, ts) in enumerate(rows):
+        a[i] = (addr, val, ts)
+    return a
+
+
+def _bank(rows):
+    a = np.zeros(len(rows), wl.BANK_DTYPE)
+    for i, r in enumerate(rows):
+        a[i] = tuple(r)
+    return a
+
+
+def _rmw(rows):
+    a = np.zeros(len(rows), wl.RMW_DTYPE)
+    for i, r in enumerate(rows):
+        a[i]["addr"] = r[:4]
+        a[i]["flags"] = r[4]
+    return a
+
+
+@pytest.mark.parametrize("name", ["bank_no_conflict.json", "bank_conflict.json",
+                                  "granule_false_sharing.json", "rmw_order.json",
+                                  "rmw_order_swapped.json"])
+def test_golden_round(name):
+    """Hand-enumerated rounds (Sec. III P1; Sec. IV-C validation, TS, merge; Sec. IV-D)."""
+    g = _golden(name)
+    start = np.array(g["start"], np.int32)
+    log = _log(g["log"])
+    ex = g["expect"]
+    if g["kind"] == "bank":
+        res = oracle.round_bank(start, _bank(g["gpu_tx"]), g["order"], g["status"], log,
+                                g["granule_bytes"], g["chunk_bytes"])
+    else:
+        res = oracle.round_rmw(start, _rmw(g["gpu_tx"]), g["order"], g["status"], log,
+                               g["granule_bytes"], g["chunk_bytes"])
+        st = np.array(g["status"])
+        assert res.out[st == 1].tolist() == [o for o, s in zip(ex["out"], g["status"]) if s == 1]
+    assert res.replayed.tolist() == ex["replayed"]
+    assert res.R.tolist() == ex["R"]
+    assert res.D.tolist() == ex["D"]
+    assert res.flags.tolist() == ex["flags"]
+    assert res.conflict == ex["conflict"]
+    assert res.final.tolist() == ex["final"]
+    assert res.ties == 0
+
+
+def test_golden_ts_freshness():
+    """Sec. IV-C: apply a tuple only if newer than the stored timestamp."""
+    g = _golden("ts_freshness.json")
+    state = np.array(g["start"], np.int32)
+    ts = np.array(g["ts_state"], np.uint32)
+    ties = oracle.cpu_image(state, ts, _log(g["log"]))
+    assert state.tolist() == g["expect"]["final"]
+    assert ts.tolist() == g["expect"]["ts_state"]
+    assert ties == g["expect"]["ties"]
+
+
+def _cache_image(g, layout):
+    img = np.zeros(layout.n_words, np.int32)
+    img[layout.key_base:layout.val_base].view(np.uint64)[:8] = g["keys"]
+    img[layout.val_base:layout.gpu_lru_base].view(np.uint64)[:8] = g["values"]
+    img[layout.gpu_lru_base:layout.gpu_lru_base + 8] = g["gpu_lru"]
+    img[layout.ver_base] = g["version"]
+    return img
+
+
+@pytest.mark.parametrize("name", ["cache_one_set.json", "cache_evict.json"])
+def test_golden_cache(name):
+    """Sec. V-D object cache: GET/PUT, per-device LRU, per-set version."""
+    g = _golden(name)
+    layout = wl.CacheLayout(log2_sets=g["log2_sets"])
+    assert layout.n_words == 49
+    img = _cache_image(g, layout)
+    reqs = np.zeros(len(g["reqs"]), wl.CACHE_DTYPE)
+    for i, (k, v, op) in enumerate(g["reqs"]):
+        reqs[i]["key"], reqs[i]["value"], reqs[i]["op"] = k, v, op
+    out, R, D = oracle.replay_cache(img, layout, reqs, g["order"], g["status"],
+                                    g["granule_bytes"], g["chunk_bytes"])
+    ex = g["expect"]
+    assert out.tolist() == ex["out"]
+    assert img[0:16].view(np.uint64).tolist() == ex["keys"]
+    assert img[16:32].view(np.uint64).tolist() == ex["values"]
+    assert img[32:40].tolist() == ex["gpu_lru"]
+    assert int(img[48]) == ex["version"]
+    assert img[40:48].tolist() == [0] * 8          # the CPU LRU region is never touched
+    assert R.tolist() == ex["R"] and D.tolist() == ex["D"]
+
+
+# ---------------------------------------------------------------------------
+# closed-form special cases (Sec. IV-C)
+# ---------------------------------------------------------------------------
+def _small_bank(seed=3, n=64, n_gpu=20, partitioned=False):
+    return wl.bank_round(seed=seed, n_accounts=n, n_gpu=n_gpu, cpu_threads=2,
+                         cpu_tx_per_thread=6, partitioned=partitioned)
+
+
+def _all_committed(n):
+    return np.arange(n, dtype=np.uint64) * 2 + 2, np.ones(n, np.uint8)
+
+
+def test_empty_cpu_log_keeps_gpu_replay():
+    """No CPU writes: validation cannot fail, final = GPU replay (Sec. IV-C)."""
+    b = _small_bank()
+    order, st = _all_committed(len(b.gpu_tx))
+    res = oracle.round_bank(b.init, b.gpu_tx, order, st, np.zeros(0, wl.LOG_DTYPE), 4, 16)
+    assert not res.conflict and res.n_conflicts == 0
+    np.testing.assert_array_equal(res.final, res.replayed)
+
+
+def test_empty_gpu_batch_gives_cpu_state():
+    """No GPU transactions: final = start + CPU image = the CPU's own replica."""
+    b = _small_bank()
+    order, st = _all_committed(0)
+    res = oracle.round_bank(b.init, b.gpu_tx[:0], order, st, b.cpu_log, 4, 16)
+    assert not res.conflict
+    np.testing.assert_array_equal(res.final, b.cpu_final)
+
+
+def test_whole_stmr_granule_always_conflicts():
+    """Granule = whole STMR, GPU read >= 1 word, log non-empty -> conflict."""
+    b = _small_bank()
+    order, st = _all_committed(len(b.gpu_tx))
+    G = 4 * b.n_accounts
+    res = oracle.round_bank(b.init, b.gpu_tx, order, st, b.cpu_log, G, G)
+    assert res.conflict and res.flags.all()
+    np.testing.assert_array_equal(res.final, b.cpu_final)
+
+
+def test_partitioned_halves_never_conflict():
+    """Sec. V-B setup: CPU and GPU on disjoint halves -> never a conflict; both kept."""
+    b = _small_bank(partitioned=True)
+    order, st = _all_committed(len(b.gpu_tx))
+    res = oracle.round_bank(b.init, b.gpu_tx, order, st, b.cpu_log, 4, 16)
+    assert not res.conflict
+    half = b.n_accounts // 2
+    np.testing.assert_array_equal(res.final[:half], b.cpu_final[:half])
+    np.testing.assert_array_equal(res.final[half:], res.replayed[half:])
+    np.testing.assert_array_equal(res.replayed[:half], b.init[:half])
+
+
+def test_every_entry_on_read_granule_sets_every_flag():
+    b = _small_bank()
+    log = b.cpu_log
+    flags, n = oracle.conflicts(log, np.unique(log["addr"] // 1), 4)
+    assert n == len(log) and flags.all()
+
+
+def test_conflict_flags_match_set_membership():
+    """Brute-force check of the flags by numpy set membership (different algorithm)."""
+    rng = np.random.default_rng(5)
+    log = np.zeros(500, wl.LOG_DTYPE)
+    log["addr"] = rng.integers(0, 4096, 500)
+    for G in (4, 64, 1024):
+        R = np.unique(rng.integers(0, 4096 * 4 // G, 40)).astype(np.uint32)
+        flags, n = oracle.conflicts(log, R, G)
+        expect = np.isin(log["addr"].astype(np.int64) * 4 // G, R)
+        assert flags.astype(bool).tolist() == expect.tolist() and n == expect.sum()
+
+
+def test_cpu_image_equals_sequential_apply_in_ts_order():
+    """Newest-ts image == applying tuples one by one in timestamp order (Sec. IV-C)."""
+    rng = np.random.default_rng(7)
+    n_words = 32
+    log = np.zeros(300, wl.LOG_DTYPE)
+    log["addr"] = rng.integers(0, n_words, 300)
+    log["value"] = rng.integers(-1000, 1000, 300)
+    log["ts"] = rng.permutation(300) + 1
+    ts0 = rng.integers(0, 150, n_words).astype(np.uint32)
+    state = rng.integers(-5, 5, n_words).astype(np.int32)
+    expect_state, expect_ts = state.copy(), ts0.copy()
+    for e in sorted(log.tolist(), key=lambda r: r[2]):
+        a, v, t = e
+        if t > expect_ts[a]:
+            expect_state[a], expect_ts[a] = v, t
+    ts = ts0.copy()
+    assert oracle.cpu_image(state, ts, log) == 0
+    np.testing.assert_array_equal(state, expect_state)
+    np.testing.assert_array_equal(ts, expect_ts)
+
+
+def test_cpu_image_counts_ties():
+    log = _log([(1, 5, 3), (1, 6, 3), (2, 1, 1)])
+    assert oracle.cpu_image(None, np.zeros(4, np.uint32), log) == 1
+
+
+# ---------------------------------------------------------------------------
+# invariants
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("partitioned", [False, True])
+def test_bank_conservation_both_outcomes(partitioned):
+    """Transfers conserve the int64 total under either outcome (bank invariant)."""
+    b = wl.bank_round(seed=11, n_accounts=1 << 12, n_gpu=3000, cpu_threads=4,
+                      cpu_tx_per_thread=300, partitioned=partitioned)
+    order, st = _all_committed(len(b.gpu_tx))
+    res = oracle.round_bank(b.init, b.gpu_tx, order, st, b.cpu_log, 4, 64)
+    assert res.conflict == (not partitioned)
+    assert oracle.sum64(res.final) == oracle.sum64(b.init) == 1000 * (1 << 12)
+    if not partitioned:
+        np.testing.assert_array_equal(res.final, b.cpu_final)
+
+
+def test_sum64_does_not_overflow():
+    x = np.full(1 << 12, 2**31 - 1, np.int32)
+    assert oracle.sum64(x) == (2**31 - 1) * (1 << 12)
+
+
+def test_rs_contains_ws_and_wrapping_arithmetic():
+    """Writes are recorded in RS (Sec. IV-C) and int32 arithmetic wraps."""
+    start = np.array([2**31 - 1, -2**31, 0, 0], np.int32)
+    tx = _bank([(0, 1, 1)])
+    res = oracle.round_bank(start, tx, [2], [1], np.zeros(0, wl.LOG_DTYPE), 4, 4)
+    assert res.replayed.tolist() == [2**31 - 2, -2**31 + 1, 0, 0]
+    tx = _bank([(1, 0, 5)])
+    r2 = oracle.round_bank(start, tx, [2], [1], np.zeros(0, wl.LOG_DTYPE), 4, 4)
+    assert r2.replayed.tolist() == [-2**31 + 4, 2**31 - 5, 0, 0]
+    assert set(r2.D.tolist()) <= set(r2.R.tolist())
+
+
+# ---------------------------------------------------------------------------
+# brute force over serial orders (P1)
+# ---------------------------------------------------------------------------
+def test_replay_follows_reported_order_bruteforce():
+    """For 3 conflicting transactions, each of the 6 orders gives its own state,
+    and the replay of order p equals a direct hand-loop execution in order p."""
+    start = np.array([3, 1, 4, 1, 5, 9, 2, 6], np.int32)
+    txs = _rmw([[0, 1, 2, 3, 1], [2, 3, 4, 5, 1], [5, 6, 7, 0, 0]])
+    seen = {}
+    for perm in itertools.permutations(range(3)):
+        order = np.zeros(3, np.uint64)
+        for rank, i in enumerate(perm):
+            order[i] = 2 * rank + 2
+        st = start.copy()
+        out, _, _ = oracle.replay_rmw(st, txs, order, np.ones(3, np.uint8), 4, 4)
+        ref = start.astype(np.int64).tolist()
+        ref_out = [0] * 3
+        for i in perm:
+            a = txs[i]["addr"].tolist()
+            s = sum(ref[x] for x in a)
+            s = ((s + 2**31) % 2**32) - 2**31
+            ref_out[i] = s
+            if txs[i]["flags"] & 1:
+                for j, x in enumerate(a):
+                    ref[x] = ((s + j + i + 2**31) % 2**32) - 2**31
+        assert st.tolist() == ref and out.tolist() == ref_out
+        seen[perm] = (tuple(st.tolist()), tuple(out.tolist()))
+    assert len(set(seen.values())) == 6
+
+
+def test_aborted_transactions_leave_no_trace():
+    """Sec. IV-B: bitmaps are updated only at commit; aborted tx are not replayed."""
+    start = np.arange(8, dtype=np.int32)
+    txs = _rmw([[0, 1, 2, 3, 1], [4, 5, 6, 7, 1]])
+    st = start.copy()
+    out, R, D = oracle.replay_rmw(st, txs, [2, 0], [1, 2], 4, 4)
+    assert R.tolist() == [0, 1, 2, 3] and D.tolist() == [0, 1, 2, 3]
+    assert st[4:].tolist() == [4, 5, 6, 7]
+
+
+# ---------------------------------------------------------------------------
+# sizing sanity of the configurations
+# ---------------------------------------------------------------------------
+def test_bank_config_expects_conflict():
+    """2^20 accounts, 65,536 GPU transfers vs 80,000 CPU writes: overlap ~ 1e4 words."""
+    b = wl.bank_round(seed=0)
+    gpu_words = np.union1d(b.gpu_tx["src"], b.gpu_tx["dst"])
+    hits = np.isin(b.cpu_log["addr"], gpu_words).sum()
+    assert len(b.cpu_log) == 80000 and 5000 < hits < 20000
+
+
+def test_validation_config_hits_exact_at_small_scale():
+    """The planted hit count is exact (2% of the log) at a reduced size."""
+    v = wl.validation_round(seed=1, log2_words=18, n_log=1 << 15)
+    flags, n = oracle.conflicts(v.log, v.read_granules, v.granule_bytes)
+    assert n == v.n_hits_planted == round(0.02 * (1 << 15))
