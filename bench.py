@@ -1,0 +1,385 @@
+"""Benchmark of the GPU side of SHeTM synchronization rounds on one B300.
+
+Step = one whole round (Sec. IV-C): a 4M-transaction W1-style batch (4 reads,
+10% also write, Zipf(0.99) addresses) runs speculatively on a 2^28-word STMR
+under the persistent executor, a 1M-tuple CPU write log (4 CPU threads) is
+validated against the read-set bitmap (64 B granules), applied with the
+newest-timestamp rule, and the winner's dirty chunks are merged into STMR^W /
+STMR^S.  value = GPU-committed transactions per second over the timed rounds,
+inputs resident in HBM; e2e = the same with the batch and the log coming from
+pinned host memory and the per-transaction results going back to it.
+
+Beside it: the validation kernel on the validation-at-scale input (2^28
+words, 16M-tuple log, 5% of granules read), in GB/s against the measured HBM
+copy peak; p50/p99 round latency; the oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the executor does not shard, so there is no data-path collective); value is
+the sum of committed transactions over the max of the ranks' times.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = ("GPU committed tx/s and p99 round latency (persistent vs per-batch); "
+          "validation GB/s vs HBM peak")
+LOG2W = 28
+N_TX = 1 << 22
+N_LOG = 1 << 20
+CPU_THREADS = 4
+GRANULE = 64
+SEED = 2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# the workload (shared by both arms)
+# ---------------------------------------------------------------------------
+def make_inputs(n_pool=2):
+    init = wl.init_stmr(SEED, 1 << LOG2W)
+    batches = [wl.rmw_batch(seed=SEED, batch=b, n_tx=N_TX, log2_words=LOG2W) for b in range(n_pool)]
+    logs = [np.concatenate(wl.cpu_write_log(SEED, r, N_LOG, LOG2W, cpu_threads=CPU_THREADS))
+            for r in range(n_pool)]
+    return init, batches, logs
+
+
+def log_for_round(logs, r):
+    """Round r reuses pool log r % pool with timestamps moved past every earlier round."""
+    lg = logs[r % len(logs)].copy()
+    lg["ts"] = lg["ts"] - lg["ts"].min() + 1 + r * N_LOG
+    return lg
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def bench_ours(args, rank, world, local_rank, inputs):
+    import torch
+
+    import paper_1905_00661_b300 as h
+    torch.cuda.set_device(local_rank)
+    hbm, peak_kind = peaks()
+    init, batches, logs = inputs
+    K, W = args.steps, args.warmup
+    ctx = h.Context(1 << LOG2W, GRANULE, {"cpu_threads": CPU_THREADS, "log_capacity": N_LOG * 2,
+                                          "cpu_log_capacity": N_LOG})
+    ctx.load(init)
+    s = ctx.stream
+    dev_tx = [torch.from_numpy(b.view(np.uint8)).cuda() for b in batches]
+    outs = [(torch.empty(N_TX, dtype=torch.int64, device="cuda"),
+             torch.empty(N_TX, dtype=torch.uint8, device="cuda"),
+             torch.empty(N_TX, dtype=torch.int32, device="cuda")) for _ in batches]
+    dev_logs = [torch.from_numpy(log_for_round(logs, r).view(np.uint8)).cuda()
+                for r in range(W + K)]
+    n_upd = [int(b["flags"].sum()) for b in batches]
+    torch.cuda.synchronize()
+
+    def one_round(r, host=None):
+        b = r % len(batches)
+        o, st_, out = outs[b]
+        if host is None:
+            ctx.log_attach(dev_logs[r])
+            tx = dev_tx[b]
+        else:
+            tx = host["dev_tx"]
+            with torch.cuda.stream(s):
+                tx.copy_(host["tx"][b], non_blocking=True)
+            lg = log_for_round(logs, r)
+            parts = np.array_split(lg, CPU_THREADS)
+            th = [threading.Thread(target=ctx.cpu_log_write, args=(t, p)) for t, p in enumerate(parts)]
+            [t.start() for t in th]
+            [t.join() for t in th]
+        ctx.submit_batch(h.HETM_WL_RMW, tx, o, st_, out, txid_base=(r * N_TX) & 0xFFFFFFFF,
+                         n_tx=N_TX)
+        st = ctx.round(stats=True)
+        if host is not None:
+            with torch.cuda.stream(s):
+                host["order"].copy_(o, non_blocking=True)
+                host["status"].copy_(st_, non_blocking=True)
+                host["out"].copy_(out, non_blocking=True)
+            s.synchronize()
+        if st["rc"] != h.HETM_OK:
+            raise RuntimeError(f"round failed: {st}")
+        st["n_upd"] = n_upd[b]
+        return st
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for r in range(W):
+        one_round(r)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with Clocks(local_rank) as clk:
+        ev0.record(s)
+        for r in range(W, W + K):
+            stats.append(one_round(r))
+        ev1.record(s)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    committed = sum(st["committed"] for st in stats)
+    # algorithmic bytes of the executor: every committed tx reads 4 words; updates also write 4
+    exec_ms = [st["ms_exec"] for st in stats]
+    exec_bytes = [16 * st["committed"] + 16 * st["n_upd"] for st in stats]
+    round_ms = [st["ms_total"] for st in stats]
+
+    # ---- e2e: host-resident inputs and results, copies inside the timed region
+    host = {"tx": [torch.from_numpy(b.view(np.uint8)).pin_memory() for b in batches],
+            "dev_tx": torch.empty(N_TX * 20, dtype=torch.uint8, device="cuda"),
+            "order": torch.empty(N_TX, dtype=torch.int64).pin_memory(),
+            "status": torch.empty(N_TX, dtype=torch.uint8).pin_memory(),
+            "out": torch.empty(N_TX, dtype=torch.int32).pin_memory()}
+    e2e_rounds = max(2, K // 2)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_commit = 0
+    for r in range(W + K, W + K + e2e_rounds):
+        e2e_commit += one_round(r, host)["committed"]
+    barrier()
+    e2e_s = time.perf_counter() - t0
+
+    # ---- validation kernel on the validation-at-scale input
+    ctx.close()
+    val = bench_validation(torch, h)
+    res = {"ms": ms, "committed": committed, "exec_ms": exec_ms, "exec_bytes": exec_bytes,
+           "round_ms": round_ms, "e2e_s": e2e_s, "e2e_commit": e2e_commit,
+           "clocks": clk.summary(), "val": val, "hbm": hbm, "peak_kind": peak_kind,
+           "aborts": sum(st["aborts"] for st in stats),
+           "gave_up": sum(st["gave_up"] for st in stats),
+           "conflict_rounds": sum(st["conflict"] for st in stats),
+           "ms_validate": float(np.mean([st["ms_validate"] for st in stats])),
+           "ms_apply": float(np.mean([st["ms_apply"] for st in stats])),
+           "ms_merge": float(np.mean([st["ms_merge"] for st in stats]))}
+    return res
+
+
+def bench_validation(torch, h, reps=20):
+    """Kernel V alone on the 16M-tuple log (12 B/tuple + 1 flag bit), 2^28 words, G = 64 B."""
+    v = wl.validation_round(seed=1, log2_words=LOG2W, with_init=False)
+    n = len(v.log)
+    with h.Context(1 << LOG2W, v.granule_bytes, {"log_capacity": 1 << 12}) as vc:
+        first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
+        vc.gpu_mark(torch.from_numpy(first).cuda())
+        dlog = torch.from_numpy(v.log.view(np.uint8)).cuda()
+        flags = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2
+        times = []
+        s = vc.stream
+        for i in range(reps + 3):
+            with torch.cuda.stream(s):
+                flush.fill_(i & 0xFF)
+                cnt.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            vc.validate_only(dlog, n, flags, cnt)
+            e1.record(s)
+            s.synchronize()
+            if i >= 3:
+                times.append(e0.elapsed_time(e1))
+        hits = int(cnt.item())
+    bytes_ = n * 12 + n / 8
+    t = float(np.mean(times))
+    return {"ms": t, "gbs": bytes_ / (t * 1e-3) / 1e9, "bytes": bytes_, "hits": hits,
+            "hits_expected": v.n_hits_planted}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline / reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(inputs, frac_tx=1 / 4):
+    """One round of the oracle on a bounded sample: the first frac of the batch
+    (serial replay in input order) and the same fraction of the CPU log."""
+    import oracle
+    init, batches, logs = inputs
+    n_tx = int(N_TX * frac_tx)
+    n_log = int(N_LOG * frac_tx)
+    tx = batches[0][:n_tx]
+    lg = log_for_round(logs, 0)[:n_log]
+    order = np.arange(n_tx, dtype=np.uint64) * 2 + 2
+    status = np.ones(n_tx, np.uint8)
+    t0 = time.perf_counter()
+    replayed = init.copy()
+    out, R, D = oracle.replay_rmw(replayed, tx, order, status, GRANULE, 16384)
+    res = oracle.round_from_replay(init, replayed, R, lg, GRANULE, np.zeros(init.size, np.uint32))
+    dt = time.perf_counter() - t0
+    return {"value": n_tx / dt, "seconds": dt, "n_tx": n_tx, "n_log": n_log,
+            "conflict": bool(res.conflict),
+            "sample": f"one round on {n_tx} of the {N_TX} transactions (input order) and "
+                      f"{n_log} of the {N_LOG} log tuples, full 2^{LOG2W}-word STMR"}
+
+
+def config_dict(world):
+    return {"workload": "rmw_round_zipf0.99_2^28w_4Mtx_1Mlog",
+            "stmr_words": 1 << LOG2W, "granule_bytes": GRANULE, "batch_tx": N_TX,
+            "update_frac": 0.1, "zipf": 0.99, "cpu_log_per_round": N_LOG,
+            "cpu_threads": CPU_THREADS, "ws_chunk_bytes": 16384,
+            "l2": "inputs larger than L2 (1 GiB STMR working copy)",
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        inputs = make_inputs(n_pool=1)
+        for _ in range(args.warmup):
+            oracle_sample(inputs, 1 / 16)
+        for _ in range(args.steps):
+            steps.append(oracle_sample(inputs, 1 / 16))
+        tx = sum(s["n_tx"] for s in steps)
+        sec = sum(s["seconds"] for s in steps)
+        v = tx / sec
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "tx/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sec / len(steps), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+                "config": config_dict(1),
+                "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "tx/s",
+                                 "sample": steps[0]["sample"]},
+                "e2e": {"value": v, "unit": "tx/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    inputs = make_inputs()
+    res = bench_ours(args, rank, world, local_rank, inputs)
+    ms, committed = res["ms"], res["committed"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, res["e2e_s"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([committed, res["e2e_commit"]], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        ms, e2e_s = float(t[0]), float(t[1])
+        committed, e2e_commit = int(c[0]), int(c[1])
+    else:
+        e2e_s, e2e_commit = res["e2e_s"], res["e2e_commit"]
+    if rank != 0:
+        return
+    cpu = oracle_sample(inputs, 1 / 4)
+    K = args.steps
+    exec_ms = float(np.mean(res["exec_ms"]))
+    exec_bytes = float(np.mean(res["exec_bytes"]))
+    achieved = exec_bytes / (exec_ms * 1e-3) / 1e9
+    val = res["val"]
+    line = {
+        "metric": METRIC, "value": committed / (ms * 1e-3), "unit": "tx/s",
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+        "data": "synthetic", "config": config_dict(world),
+        "p50_round_ms": float(np.percentile(res["round_ms"], 50)),
+        "p99_round_ms": float(np.percentile(res["round_ms"], 99)),
+        "phase_ms": {"exec": exec_ms, "validate": res["ms_validate"], "apply": res["ms_apply"],
+                     "merge": res["ms_merge"]},
+        "aborts": res["aborts"], "gave_up": res["gave_up"],
+        "conflict_rounds": res["conflict_rounds"],
+        "roofline": {"kernel": "k_exec", "bound": "hbm", "achieved": achieved,
+                     "peak": res["hbm"], "unit": "GB/s", "frac": achieved / res["hbm"],
+                     "peak_kind": res["peak_kind"], "traffic": None,
+                     "bytes_per_launch": exec_bytes},
+        "validation": {"kernel": "k_validate_direct", "ms": val["ms"], "gbs": val["gbs"],
+                       "frac": val["gbs"] / res["hbm"], "bytes": val["bytes"],
+                       "hits": val["hits"], "hits_expected": val["hits_expected"],
+                       "workload": "validation_2^28w_16Mlog_g64"},
+        "e2e": {"value": e2e_commit / e2e_s, "unit": "tx/s",
+                "h2d_bytes_per_step": N_TX * 20 + N_LOG * 12,
+                "d2h_bytes_per_step": N_TX * (8 + 1 + 4)},
+        "gpu_launches": 4 * K,
+        "clocks": res["clocks"],
+        "cpu_baseline": {"value": cpu["value"], "unit": "tx/s", "cores": 1, "kind": "oracle",
+                         "sample": cpu["sample"]},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,265 @@
+/*
+ * hetm.h -- C ABI of the GPU side of a Speculative HeTM (SHeTM)
+ * synchronization round, after Castro, Romano, Ilic and Khan, "HeTM:
+ * Transactional Memory for Heterogeneous Systems" (arXiv 1905.00661).
+ *
+ * A round (Sec. IV-C) has three phases:
+ *   execution  -- GPU transaction batches run speculatively on the working
+ *                 copy STMR^W; every commit ORs the granules it read or wrote
+ *                 into RS_bmp and the transfer chunks it wrote into WS_bmp
+ *                 (Sec. IV-B "GPU instrumentation"; writes also go to RS_bmp,
+ *                 Sec. IV-C, so one test covers write-write conflicts);
+ *   validation -- the CPU write-set log of <addr, value, ts> tuples, shipped
+ *                 to the device in chunks (Sec. IV-D), is tested against
+ *                 RS_bmp; a hit marks the round as conflicting, and every
+ *                 tuple is applied anyway to STMR^W and the shadow STMR^S when
+ *                 its timestamp is the newest for its word (array TS);
+ *   merge      -- the chunks marked in WS_bmp are copied W -> S when
+ *                 validation succeeded and S -> W when it failed, undoing the
+ *                 GPU batch (GPU-loses policy, Sec. IV-C; shadow-copy
+ *                 rollback, Sec. IV-D).  Afterwards W == S.
+ *
+ * Conventions for every call:
+ *   - return 0 (HETM_OK) or a negative HETM_E* code; hetm_strerror() names it;
+ *   - "device pointer" = memory of the context's CUDA device (cudaMalloc,
+ *     a torch CUDA tensor's data_ptr(), ...); "host pointer" = any host
+ *     memory unless stated as pinned;
+ *   - the library never takes ownership of caller memory; caller device
+ *     buffers passed to an asynchronous call must stay valid until that
+ *     work has completed on the context stream (hetm_sync);
+ *   - one controller thread drives a context; only hetm_cpu_log_write may be
+ *     called concurrently, from distinct `thread` ids.
+ */
+#ifndef HETM_H
+#define HETM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HETM_API __attribute__((visibility("default")))
+#else
+#define HETM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define HETM_OK 0
+#define HETM_EINVAL (-1)    /* bad argument or precondition violated          */
+#define HETM_ENOMEM (-2)    /* device or pinned host allocation failed        */
+#define HETM_ECAPACITY (-3) /* a fixed-capacity buffer or table is full       */
+#define HETM_ETIMEOUT (-4)  /* a bounded device wait gave up                  */
+#define HETM_ECUDA (-5)     /* a CUDA runtime call failed                     */
+#define HETM_EBUSY (-6)     /* not admitted now (memory or slots); retry later */
+#define HETM_EDEVICE (-7)   /* a kernel met an out-of-range address; the
+                               offending item was skipped, state is undefined */
+
+HETM_API const char *hetm_strerror(int code);
+
+/* --------------------------------------------------------------- records */
+/* CPU write-set log tuple (Sec. IV-B, CPU instrumentation).  12 bytes,
+ * packed.  `ts` totally orders the writes to one word: it must be >= 1 and
+ * unique per word over the lifetime of the context (ties and repeats are an
+ * invalid input; which of two tied tuples wins is unspecified). */
+typedef struct hetm_log_entry {
+    uint32_t addr;  /* word index into the STMR, < stmr_words */
+    int32_t value;  /* value the CPU transaction wrote          */
+    uint32_t ts;    /* commit timestamp of the CPU transaction  */
+} hetm_log_entry;
+
+/* Transactional workloads run by the GPU executor. */
+#define HETM_WL_BANK 1  /* hetm_bank_tx                      */
+#define HETM_WL_RMW 2   /* hetm_rmw_tx (W1 of Sec. V-A)       */
+#define HETM_WL_CACHE 3 /* hetm_cache_req (Sec. V-D)          */
+
+/* bank transfer: bal[src] -= amount; bal[dst] += amount (int32, wrapping).
+ * Accounts are words base+src, base+dst with base = hetm_batch.word_base. */
+typedef struct hetm_bank_tx {
+    uint32_t src, dst;
+    int32_t amount;
+} hetm_bank_tx;
+
+/* Four word reads; with flags bit 0 set the transaction also writes
+ * s + j + txid to its j-th word, s = the 32-bit sum it read, txid =
+ * hetm_batch.txid_base + index.  out (int32) receives s. */
+typedef struct hetm_rmw_tx {
+    uint32_t addr[4];
+    uint32_t flags;
+} hetm_rmw_tx;
+
+/* Object-cache request, op 0 = GET, 1 = PUT.  Set = SplitMix64 finalizer of
+ * key mod 2^cache_log2_sets.  GET hit: out = value and the GPU LRU stamp of
+ * the slot is set to the commit version; miss: out = UINT64_MAX.  PUT: hit
+ * way, else the first empty way (key 0), else the way with the smallest GPU
+ * LRU stamp (lowest way on ties) takes key and value, its stamp becomes the
+ * commit version and the set version word is incremented; out = way. */
+typedef struct hetm_cache_req {
+    uint64_t key;
+    uint64_t value;
+    uint32_t op;
+    uint32_t pad;
+} hetm_cache_req;
+
+/* ---------------------------------------------------------- configuration */
+typedef struct hetm_config {
+    uint32_t ws_chunk_bytes;   /* WS_bmp / merge chunk, power of two >= 16
+                                  (Sec. IV-D uses 16 KB); default 16384    */
+    uint32_t lock_log2;        /* 2^lock_log2 striped version locks; 22   */
+    uint32_t lock_shift;       /* words per lock stripe = 2^lock_shift; 0  */
+    uint32_t exec_blocks;      /* executor grid; 0 = one wave (SMs x occ.) */
+    uint32_t exec_threads;     /* executor block size (multiple of 32); 256 */
+    uint32_t max_attempts;     /* per-transaction attempt bound; 1<<20     */
+    uint32_t cpu_threads;      /* number of per-thread CPU logs; 8         */
+    uint32_t log_chunk_bytes;  /* H2D shipping chunk, multiple of 12; 49152 */
+    uint64_t log_capacity;     /* device log entries per round; 1<<24      */
+    uint64_t cpu_log_capacity; /* pinned entries per CPU thread per round; 1<<22 */
+    uint32_t max_batches;      /* pending batches per round; 4096          */
+    uint32_t cache_log2_sets;  /* object-cache layout (HETM_WL_CACHE)      */
+    uint64_t cache_key_base, cache_val_base, cache_lru_base, cache_ver_base;
+    /* Optional device allocator (e.g. a framework's caching allocator);
+     * NULL = cudaMalloc/cudaFree.  Called only from hetm_init/hetm_destroy. */
+    void *(*dev_alloc)(size_t bytes, void *user);
+    void (*dev_free)(void *ptr, void *user);
+    void *alloc_user;
+} hetm_config;
+
+/* Fill *cfg with the defaults listed above. */
+HETM_API int hetm_config_default(hetm_config *cfg);
+
+/* ------------------------------------------------------------- lifecycle */
+typedef struct hetm_ctx hetm_ctx;
+
+/* Create a context on the current CUDA device for an STMR of `stmr_words`
+ * int32 words (1 <= stmr_words < 2^32) with conflict granule
+ * `granule_bytes` (power of two, >= 4; Sec. V-A studies 4 B and 1 KB).
+ * Allocates STMR^W, STMR^S, TS, RS_bmp, WS_bmp, the lock table, two device
+ * log buffers and the pinned per-thread CPU logs.  `stream` is a
+ * cudaStream_t for all device work (NULL = a new non-blocking stream owned
+ * by the context).  cfg NULL = defaults.  On success *out owns everything. */
+HETM_API int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes,
+              const hetm_config *cfg, void *stream);
+
+/* Release every resource of the context (synchronizes its streams). */
+HETM_API void hetm_destroy(hetm_ctx *ctx);
+
+/* STMR^W = STMR^S = src[0..n), TS = 0, bitmaps and logs cleared.  src is a
+ * host or device pointer (n == stmr_words).  Synchronous. */
+HETM_API int hetm_load(hetm_ctx *ctx, const int32_t *src, uint64_t n);
+
+/* Copy n words from offset `off` of STMR^W (which = 0) or STMR^S
+ * (which = 1) to host memory.  Synchronizes the context stream. */
+HETM_API int hetm_read_stmr(hetm_ctx *ctx, int which, int32_t *host_dst, uint64_t off, uint64_t n);
+
+/* Device address of STMR^W (0), STMR^S (1), TS (2), RS_bmp (3), WS_bmp (4);
+ * NULL for other values.  Borrowed: valid until hetm_destroy. */
+HETM_API void *hetm_device_ptr(hetm_ctx *ctx, int which);
+
+/* Size in 32-bit words of RS_bmp and WS_bmp (bit g of word g/32, LSB first). */
+HETM_API int hetm_bitmap_words(hetm_ctx *ctx, uint64_t *rs_words, uint64_t *ws_words);
+
+/* Wait for all work queued on the context stream. */
+HETM_API int hetm_sync(hetm_ctx *ctx);
+
+/* -------------------------------------------------- execution phase (A1) */
+/* One transaction batch.  All pointers are device pointers; outputs may be
+ * NULL.  order[i] is the commit key of transaction i: sorting the committed
+ * transactions by (order, index) gives a serial order that reproduces
+ * STMR^W and every output (property P1, Sec. III).  An update commit has
+ * key 2v (v = its commit version, unique); a read-only commit has key
+ * 2v'+1 where v' is the newest version it observed.  status[i] = 1
+ * committed, 2 gave up after max_attempts (no effect, no bitmap bits). */
+typedef struct hetm_batch {
+    uint32_t workload;   /* HETM_WL_* */
+    uint32_t n_tx;
+    const void *tx;      /* n_tx records of the workload's type            */
+    uint64_t *order;     /* out: commit key per transaction                */
+    uint8_t *status;     /* out: 1 committed, 2 gave up                    */
+    void *out;           /* out: int32 (RMW) or uint64 (cache) per tx      */
+    uint32_t txid_base;  /* RMW: txid = txid_base + index                   */
+    uint32_t word_base;  /* BANK: account a is word word_base + a           */
+} hetm_batch;
+
+/* Admit a batch into the current round's execution phase.  The batch is
+ * queued; hetm_gpu_exec (or hetm_round) runs every queued batch in one
+ * persistent launch.  Returns HETM_EBUSY when the batch table is full or
+ * the device lacks `reserve_bytes` of free memory for its buffers.  With
+ * cfg->max_batches reached, call hetm_gpu_exec first.  *batch_id gets a
+ * context-unique id. */
+HETM_API int hetm_gpu_submit_batch(hetm_ctx *ctx, const hetm_batch *batch, uint64_t *batch_id);
+
+/* Run every queued batch now: one launch of the persistent executor that
+ * drains all of them (uneven sizes), asynchronous on the context stream.
+ * per_batch != 0 instead launches the executor once per batch. */
+HETM_API int hetm_gpu_exec(hetm_ctx *ctx, int per_batch);
+
+/* Execution statistics since the last hetm_load: committed transactions,
+ * transactions that gave up, and aborted attempts.  Synchronizes. */
+HETM_API int hetm_exec_counters(hetm_ctx *ctx, uint64_t *committed, uint64_t *gave_up, uint64_t *aborts);
+
+/* Non-transactional instrumentation of words the GPU read (vals NULL) or
+ * wrote (STMR^W[addr[i]] = vals[i]) -- a planted GPU batch.  Device
+ * pointers, asynchronous. */
+HETM_API int hetm_gpu_mark(hetm_ctx *ctx, const uint32_t *addr, const int32_t *vals, uint64_t n);
+
+/* ---------------------------------------------------- log shipping (A2) */
+/* Append n tuples (host memory) to CPU thread `thread`'s pinned log.  Each
+ * full log_chunk_bytes chunk is copied to the device log with
+ * cudaMemcpyAsync on a side stream right away, overlapping the GPU's work
+ * (Sec. IV-D).  Thread-safe for distinct `thread` values.  HETM_ECAPACITY
+ * if the thread's pinned log or the device log would overflow. */
+HETM_API int hetm_cpu_log_write(hetm_ctx *ctx, uint32_t thread, const hetm_log_entry *e, uint32_t n);
+
+/* Use caller device memory as this round's CPU log instead of the shipped
+ * one (no copy).  `dev_log` must be 16-byte aligned and stay valid until the
+ * round's validation has completed. */
+HETM_API int hetm_log_attach(hetm_ctx *ctx, const hetm_log_entry *dev_log, uint64_t n);
+
+/* ------------------------------------------------- validation (A3..A5) */
+/* Ship the rest of the CPU logs, then validate them against RS_bmp and
+ * apply every tuple whose timestamp is the newest for its word and newer
+ * than TS to STMR^W and STMR^S (Sec. IV-C).  dev_flag_bits (device, may be
+ * NULL) receives bit i = "tuple i of the device log hit a read granule",
+ * ceil(n/32) words.  If n_conflicts is non-NULL the call synchronizes and
+ * stores the number of hits; otherwise the count stays on the device for
+ * hetm_merge(ctx, -1). */
+HETM_API int hetm_validate(hetm_ctx *ctx, uint64_t *n_conflicts, uint32_t *dev_flag_bits);
+
+/* Validation only (no apply) of a device log: the early-validation test of
+ * Sec. IV-D.  Asynchronous; *dev_count (device uint64) is incremented by
+ * the number of hits, flags as in hetm_validate (may be NULL). */
+HETM_API int hetm_validate_only(hetm_ctx *ctx, const hetm_log_entry *dev_log, uint64_t n,
+                       uint32_t *dev_flag_bits, uint64_t *dev_count);
+
+/* -------------------------------------------------------- merge (A6) */
+/* Copy the WS_bmp chunks W -> S (conflict == 0) or S -> W (conflict == 1);
+ * conflict == -1 takes the decision from the last hetm_validate on the
+ * device, without a host round trip.  Then clears RS_bmp and WS_bmp. */
+HETM_API int hetm_merge(hetm_ctx *ctx, int conflict);
+
+/* ------------------------------------------------------ round (A1..A7) */
+typedef struct hetm_round_stats {
+    uint64_t n_log;          /* CPU tuples validated                     */
+    uint64_t n_conflicts;    /* tuples that hit RS_bmp                    */
+    int32_t conflict;        /* 1: GPU batch undone                       */
+    int32_t err;             /* HETM_OK or HETM_EDEVICE                   */
+    uint64_t committed;      /* GPU transactions committed this round     */
+    uint64_t gave_up;        /* GPU transactions that gave up             */
+    uint64_t aborts;         /* aborted GPU attempts this round           */
+    uint64_t dirty_chunks;   /* WS_bmp chunks merged                      */
+    uint32_t n_batches;      /* batches executed this round               */
+    float ms_exec, ms_validate, ms_apply, ms_merge, ms_total;
+} hetm_round_stats;
+
+/* One whole round: run the queued batches (persistent executor), ship the
+ * CPU logs, validate, apply, merge, clear.  The device part is a CUDA graph
+ * captured on first use and replayed.  stats NULL = asynchronous (no host
+ * synchronization); otherwise waits and fills *stats. */
+HETM_API int hetm_round(hetm_ctx *ctx, hetm_round_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HETM_H */

@@ -1,0 +1,323 @@
+"""Python binding of libhetm.so -- the GPU side of a SHeTM synchronization round.
+
+Argument marshalling only: every step of the round runs in the CUDA library
+(``csrc/``), whose C ABI is ``include/hetm.h``.  PyTorch supplies device
+memory (the context allocates through torch's caching allocator) and streams
+(each context owns a torch CUDA stream, ordered against the caller's current
+stream on every call).  There is no CPU fallback: importing this package
+without the built library, or using it without a CUDA device, raises.
+
+The module-level ``hetm_*`` functions carry the C names; ``Context`` is the
+same API on an object.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhetm.so")
+
+HETM_OK, HETM_EINVAL, HETM_ENOMEM, HETM_ECAPACITY = 0, -1, -2, -3
+HETM_ETIMEOUT, HETM_ECUDA, HETM_EBUSY, HETM_EDEVICE = -4, -5, -6, -7
+HETM_WL_BANK, HETM_WL_RMW, HETM_WL_CACHE = 1, 2, 3
+STMR_W, STMR_S, TS, RS_BMP, WS_BMP = 0, 1, 2, 3, 4
+
+LOG_DTYPE = np.dtype([("addr", "<u4"), ("value", "<i4"), ("ts", "<u4")])
+
+_vp, _u32, _u64, _i32, _int = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                               ctypes.c_int32, ctypes.c_int)
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class hetm_config(ctypes.Structure):
+    _fields_ = [("ws_chunk_bytes", _u32), ("lock_log2", _u32), ("lock_shift", _u32),
+                ("exec_blocks", _u32), ("exec_threads", _u32), ("max_attempts", _u32),
+                ("cpu_threads", _u32), ("log_chunk_bytes", _u32), ("log_capacity", _u64),
+                ("cpu_log_capacity", _u64), ("max_batches", _u32), ("cache_log2_sets", _u32),
+                ("cache_key_base", _u64), ("cache_val_base", _u64), ("cache_lru_base", _u64),
+                ("cache_ver_base", _u64), ("dev_alloc", _ALLOC), ("dev_free", _FREE),
+                ("alloc_user", _vp)]
+
+
+class hetm_batch(ctypes.Structure):
+    _fields_ = [("workload", _u32), ("n_tx", _u32), ("tx", _vp), ("order", _vp), ("status", _vp),
+                ("out", _vp), ("txid_base", _u32), ("word_base", _u32)]
+
+
+class hetm_round_stats(ctypes.Structure):
+    _fields_ = [("n_log", _u64), ("n_conflicts", _u64), ("conflict", _i32), ("err", _i32),
+                ("committed", _u64), ("gave_up", _u64), ("aborts", _u64), ("dirty_chunks", _u64),
+                ("n_batches", _u32), ("ms_exec", ctypes.c_float), ("ms_validate", ctypes.c_float),
+                ("ms_apply", ctypes.c_float), ("ms_merge", ctypes.c_float),
+                ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+#: every symbol include/hetm.h declares
+SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", "hetm_load",
+           "hetm_read_stmr", "hetm_device_ptr", "hetm_bitmap_words", "hetm_sync",
+           "hetm_gpu_submit_batch", "hetm_gpu_exec", "hetm_exec_counters", "hetm_gpu_mark",
+           "hetm_cpu_log_write", "hetm_log_attach", "hetm_validate", "hetm_validate_only",
+           "hetm_merge", "hetm_round")
+
+
+class HetmError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {code} ({strerror(code)})")
+
+
+def _declare(L):
+    P = ctypes.POINTER
+    sig = {
+        "hetm_strerror": (ctypes.c_char_p, [_int]),
+        "hetm_config_default": (_int, [P(hetm_config)]),
+        "hetm_init": (_int, [P(_vp), _u64, _u32, P(hetm_config), _vp]),
+        "hetm_destroy": (None, [_vp]),
+        "hetm_load": (_int, [_vp, _vp, _u64]),
+        "hetm_read_stmr": (_int, [_vp, _int, _vp, _u64, _u64]),
+        "hetm_device_ptr": (_vp, [_vp, _int]),
+        "hetm_bitmap_words": (_int, [_vp, P(_u64), P(_u64)]),
+        "hetm_sync": (_int, [_vp]),
+        "hetm_gpu_submit_batch": (_int, [_vp, P(hetm_batch), P(_u64)]),
+        "hetm_gpu_exec": (_int, [_vp, _int]),
+        "hetm_exec_counters": (_int, [_vp, P(_u64), P(_u64), P(_u64)]),
+        "hetm_gpu_mark": (_int, [_vp, _vp, _vp, _u64]),
+        "hetm_cpu_log_write": (_int, [_vp, _u32, _vp, _u32]),
+        "hetm_log_attach": (_int, [_vp, _vp, _u64]),
+        "hetm_validate": (_int, [_vp, P(_u64), _vp]),
+        "hetm_validate_only": (_int, [_vp, _vp, _u64, _vp, _vp]),
+        "hetm_merge": (_int, [_vp, _int]),
+        "hetm_round": (_int, [_vp, P(hetm_round_stats)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    return L
+
+
+def load_library(path: str = LIB_PATH):
+    """ctypes handle of the library; raises if it has not been built."""
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python paper_1905_00661_b300/build.py`")
+    return _declare(ctypes.CDLL(path))
+
+
+_lib = load_library()
+
+
+def lib():
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return _lib.hetm_strerror(code).decode()
+
+
+def _ck(rc, what):
+    if rc != HETM_OK:
+        raise HetmError(rc, what)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------
+def hetm_config_default() -> hetm_config:
+    cfg = hetm_config()
+    _ck(_lib.hetm_config_default(ctypes.byref(cfg)), "hetm_config_default")
+    return cfg
+
+
+def hetm_init(stmr_words, granule_bytes, cfg=None, stream=None):
+    h = _vp()
+    _ck(_lib.hetm_init(ctypes.byref(h), stmr_words, granule_bytes,
+                       ctypes.byref(cfg) if cfg is not None else None, stream), "hetm_init")
+    return h
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous(), "tensors passed to the library must be contiguous"
+    return x.data_ptr()
+
+
+class _CudaArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+# ---------------------------------------------------------------------------
+# object API
+# ---------------------------------------------------------------------------
+class Context:
+    """One STMR replica on the GPU plus the state of its synchronization rounds."""
+
+    def __init__(self, stmr_words: int, granule_bytes: int, config: dict | None = None,
+                 torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the SHeTM round library needs a CUDA device")
+        self.torch = torch
+        self.n_words = int(stmr_words)
+        self.granule_bytes = int(granule_bytes)
+        self.stream = torch.cuda.Stream()
+        cfg = hetm_config_default()
+        for k, v in (config or {}).items():
+            setattr(cfg, k, v)
+        self._cb = None
+        if torch_allocator:
+            dev = torch.cuda.current_device()
+            stream = self.stream
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+                except Exception:
+                    return None
+
+            def _free(p, user):
+                torch.cuda.caching_allocator_delete(p)
+
+            self._cb = (_ALLOC(_alloc), _FREE(_free))
+            cfg.dev_alloc, cfg.dev_free = self._cb
+        self.config = cfg
+        self.h = hetm_init(self.n_words, self.granule_bytes, cfg, self.stream.cuda_stream)
+        rw, ww = _u64(), _u64()
+        _ck(_lib.hetm_bitmap_words(self.h, ctypes.byref(rw), ctypes.byref(ww)), "hetm_bitmap_words")
+        self.rs_words, self.ws_words = rw.value, ww.value
+
+    # stream ordering against the caller's torch stream
+    def _enter(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def _leave(self):
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.hetm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------- state
+    def load(self, src):
+        """STMR^W = STMR^S = src (numpy int32 or CUDA int32 tensor); TS and bitmaps cleared."""
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.int32)
+        else:
+            self._enter()
+        _ck(_lib.hetm_load(self.h, _ptr(src), len(src)), "hetm_load")
+
+    def read_stmr(self, which=STMR_W, off=0, n=None) -> np.ndarray:
+        n = self.n_words - off if n is None else n
+        out = np.empty(n, np.int32)
+        _ck(_lib.hetm_read_stmr(self.h, which, out.ctypes.data, off, n), "hetm_read_stmr")
+        return out
+
+    def device_tensor(self, which):
+        """Zero-copy torch view of STMR^W, STMR^S, TS, RS_bmp or WS_bmp."""
+        p = _lib.hetm_device_ptr(self.h, which)
+        n = {STMR_W: self.n_words, STMR_S: self.n_words, TS: self.n_words,
+             RS_BMP: self.rs_words, WS_BMP: self.ws_words}[which]
+        ts = "<i4" if which in (STMR_W, STMR_S) else "<u4"
+        t = self.torch.as_tensor(_CudaArray(p, n, ts), device="cuda")
+        return t
+
+    def sync(self):
+        _ck(_lib.hetm_sync(self.h), "hetm_sync")
+
+    # ------------------------------------------------------------- execution
+    def submit_batch(self, workload, tx, order=None, status=None, out=None, txid_base=0,
+                     word_base=0, n_tx=None) -> int:
+        b = hetm_batch(workload, int(len(tx) if n_tx is None else n_tx), _ptr(tx), _ptr(order),
+                       _ptr(status), _ptr(out), txid_base, word_base)
+        bid = _u64()
+        _ck(_lib.hetm_gpu_submit_batch(self.h, ctypes.byref(b), ctypes.byref(bid)),
+            "hetm_gpu_submit_batch")
+        return bid.value
+
+    def gpu_exec(self, per_batch=False):
+        self._enter()
+        _ck(_lib.hetm_gpu_exec(self.h, int(per_batch)), "hetm_gpu_exec")
+        self._leave()
+
+    def exec_counters(self):
+        c, g, a = _u64(), _u64(), _u64()
+        rc = _lib.hetm_exec_counters(self.h, ctypes.byref(c), ctypes.byref(g), ctypes.byref(a))
+        return {"committed": c.value, "gave_up": g.value, "aborts": a.value, "rc": rc}
+
+    def gpu_mark(self, addr, vals=None):
+        self._enter()
+        _ck(_lib.hetm_gpu_mark(self.h, _ptr(addr), _ptr(vals), len(addr)), "hetm_gpu_mark")
+        self._leave()
+
+    # ------------------------------------------------------------- CPU logs
+    def cpu_log_write(self, thread, entries: np.ndarray):
+        e = np.ascontiguousarray(entries)
+        assert e.dtype.itemsize == 12
+        _ck(_lib.hetm_cpu_log_write(self.h, thread, e.ctypes.data, len(e)), "hetm_cpu_log_write")
+
+    def log_attach(self, dev_log, n=None):
+        n = dev_log.numel() * dev_log.element_size() // 12 if n is None else n
+        _ck(_lib.hetm_log_attach(self.h, _ptr(dev_log), n), "hetm_log_attach")
+
+    # ------------------------------------------------------------- validation / merge
+    def validate(self, flags=None, sync=True):
+        self._enter()
+        n = _u64()
+        _ck(_lib.hetm_validate(self.h, ctypes.byref(n) if sync else None, _ptr(flags)),
+            "hetm_validate")
+        self._leave()
+        return n.value if sync else None
+
+    def validate_only(self, dev_log, n, flags=None, count=None):
+        self._enter()
+        _ck(_lib.hetm_validate_only(self.h, _ptr(dev_log), n, _ptr(flags), _ptr(count)),
+            "hetm_validate_only")
+        self._leave()
+
+    def merge(self, conflict=-1):
+        self._enter()
+        _ck(_lib.hetm_merge(self.h, int(conflict)), "hetm_merge")
+        self._leave()
+
+    def round(self, stats=True):
+        self._enter()
+        if stats:
+            st = hetm_round_stats()
+            rc = _lib.hetm_round(self.h, ctypes.byref(st))
+            self._leave()
+            d = st.as_dict()
+            d["rc"] = rc
+            if rc not in (HETM_OK, HETM_EDEVICE, HETM_ETIMEOUT):
+                raise HetmError(rc, "hetm_round")
+            return d
+        _ck(_lib.hetm_round(self.h, None), "hetm_round")
+        self._leave()
+        return None

@@ -1,0 +1,747 @@
+// Host runtime and C ABI of the SHeTM round library.
+//
+// Owns the device state of one STMR (working copy W, shadow S, timestamp
+// array TS, RS_bmp, WS_bmp, lock table, device log buffers), the pinned
+// per-thread CPU logs and their H2D shipping on a side stream, the batch
+// table of the current execution phase, and two captured CUDA graphs: the
+// persistent executor launch and the validate -> apply -> merge -> clear
+// chain (Sec. IV-C, IV-D).
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "hetm_internal.cuh"
+
+using namespace hetm;
+
+namespace {
+
+struct Scratch {                    // device-resident counters
+    unsigned long long gv;          // commit-version clock
+    unsigned long long next;        // executor work counter
+    unsigned long long counters[3]; // committed, gave up, aborts (cumulative)
+    unsigned long long conflicts;   // hits of the last validation
+    unsigned long long dirty;       // chunks merged by the last merge
+    int err;
+    int pad;
+};
+
+struct RoundOut {                   // pinned copy of the round's results
+    unsigned long long counters[3];
+    unsigned long long conflicts;
+    unsigned long long dirty;
+    int err;
+    int pad;
+};
+
+struct ThreadLog {
+    std::mutex mu;
+    hetm_log_entry *buf[2] = {nullptr, nullptr};  // pinned, alternating rounds
+    int cur = 0;
+    uint64_t fill = 0;     // tuples written into buf[cur]
+    uint64_t shipped = 0;  // tuples of buf[cur] already queued for H2D
+};
+
+int ilog2(uint64_t v) {
+    int r = 0;
+    while ((1ull << r) < v) ++r;
+    return r;
+}
+
+bool pow2(uint64_t v) { return v && !(v & (v - 1)); }
+
+}  // namespace
+
+struct hetm_ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t ship = nullptr;
+    hetm_config cfg{};
+    uint64_t n_words = 0;
+    uint32_t granule_bytes = 0, gshift = 0, cshift = 0;
+    uint64_t rs_words = 0, ws_words = 0;
+
+    int32_t *W = nullptr, *S = nullptr;
+    uint32_t *TS = nullptr, *rs = nullptr, *ws = nullptr;
+    unsigned long long *locks = nullptr;
+    Scratch *scr = nullptr;
+    DevRound *d_round = nullptr;   // [0] fused round, [1 + b] batch b alone
+    DevBatch *d_batches = nullptr;
+    uint64_t *d_prefix = nullptr;
+    uint64_t *d_prefix0 = nullptr; // {0} for single-batch launches
+    hetm_log_entry *dlog[2] = {nullptr, nullptr};
+
+    // pinned staging of the batch table (two slots, alternating)
+    struct Stage {
+        DevRound *rounds = nullptr;
+        DevBatch *batches = nullptr;
+        uint64_t *prefix = nullptr;
+        cudaEvent_t used = nullptr;
+    } stage[2];
+    int stage_cur = 0;
+    RoundOut *out = nullptr;       // pinned
+
+    std::vector<DevBatch> pending;
+    uint64_t next_batch_id = 1;
+
+    // CPU logs
+    std::vector<std::unique_ptr<ThreadLog>> tlogs;
+    std::atomic<uint64_t> dlog_fill{0};
+    int dlog_cur = 0;
+    cudaEvent_t dlog_free[2] = {nullptr, nullptr};  // last validation that read dlog[i]
+    cudaEvent_t ship_done = nullptr;
+    cudaEvent_t tlog_free[2] = {nullptr, nullptr};  // copies out of host buffers i
+    const hetm_log_entry *attached = nullptr;
+    uint64_t attached_n = 0;
+    std::atomic<int> ship_err{0};
+
+    // graphs
+    cudaGraphExec_t g_exec = nullptr, g_sync = nullptr;
+    cudaEvent_t ev[7] = {};  // round timing: 0/6 around the executor, 1..4 in the sync graph, 5 end
+
+    int exec_blocks = 0, exec_threads = 256, stream_blocks = 0;
+    unsigned long long prev_counters[3] = {0, 0, 0};
+
+    std::vector<void *> dev_allocs;
+};
+
+#define CK(x)                                                                       \
+    do {                                                                            \
+        cudaError_t e_ = (x);                                                       \
+        if (e_ != cudaSuccess) {                                                    \
+            std::fprintf(stderr, "hetm: %s failed: %s (%s:%d)\n", #x,              \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);               \
+            return HETM_ECUDA;                                                      \
+        }                                                                           \
+    } while (0)
+
+namespace {
+
+void *dev_alloc(hetm_ctx *c, size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->cfg.dev_alloc) {
+        p = c->cfg.dev_alloc(bytes, c->cfg.alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->dev_allocs.push_back(p);
+    return p;
+}
+
+template <class T>
+bool dev_alloc_t(hetm_ctx *c, T **p, size_t count) {
+    *p = static_cast<T *>(dev_alloc(c, count * sizeof(T)));
+    return *p != nullptr;
+}
+
+template <class T>
+bool host_alloc_t(T **p, size_t count) {
+    if (cudaHostAlloc(reinterpret_cast<void **>(p), std::max<size_t>(count * sizeof(T), 16),
+                      cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+// Queue k tuples of thread log L for H2D at the device log's next free slot.
+int ship_locked(hetm_ctx *c, ThreadLog &L, uint64_t k) {
+    if (k == 0) return HETM_OK;
+    uint64_t off = c->dlog_fill.fetch_add(k);
+    if (off + k > c->cfg.log_capacity) {
+        c->dlog_fill.fetch_sub(k);
+        return HETM_ECAPACITY;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->dlog[c->dlog_cur] + off, L.buf[L.cur] + L.shipped,
+                                    k * sizeof(hetm_log_entry), cudaMemcpyHostToDevice, c->ship);
+    if (e != cudaSuccess) {
+        c->ship_err.store(HETM_ECUDA);
+        return HETM_ECUDA;
+    }
+    L.shipped += k;
+    return HETM_OK;
+}
+
+// End the CPU side of a round: ship every partial chunk, switch every thread
+// to its other host buffer and the device log to its other buffer.  On
+// return *log / *n describe the round's device log; c->ship_done follows
+// the last copy.
+int flush_logs(hetm_ctx *c, const hetm_log_entry **log, uint64_t *n) {
+    std::vector<std::unique_lock<std::mutex>> held;
+    held.reserve(c->tlogs.size());
+    for (auto &L : c->tlogs) held.emplace_back(L->mu);
+    int rc = HETM_OK;
+    for (auto &Lp : c->tlogs) {
+        ThreadLog &L = *Lp;
+        if (L.buf[L.cur]) {
+            int r = ship_locked(c, L, L.fill - L.shipped);
+            if (r != HETM_OK) rc = r;
+        }
+    }
+    if (c->ship_err.load() != HETM_OK) rc = c->ship_err.exchange(HETM_OK);
+    const int hb = c->tlogs.empty() ? 0 : c->tlogs[0]->cur;
+    CK(cudaEventRecord(c->tlog_free[hb], c->ship));
+    CK(cudaEventRecord(c->ship_done, c->ship));
+    if (c->attached) {
+        *log = c->attached;
+        *n = c->attached_n;
+    } else {
+        *log = c->dlog[c->dlog_cur];
+        *n = c->dlog_fill.load();
+    }
+    c->attached = nullptr;
+    c->attached_n = 0;
+    // next round: the other buffers; wait until the copies out of the other
+    // host buffer (issued two rounds ago) are done before refilling it
+    CK(cudaEventSynchronize(c->tlog_free[hb ^ 1]));
+    for (auto &Lp : c->tlogs) {
+        Lp->cur ^= 1;
+        Lp->fill = 0;
+        Lp->shipped = 0;
+    }
+    c->dlog_cur ^= 1;
+    c->dlog_fill.store(0);
+    // the other device buffer is refilled only after the validation that
+    // last read it
+    CK(cudaStreamWaitEvent(c->ship, c->dlog_free[c->dlog_cur], 0));
+    return rc;
+}
+
+// Stage the pending batch table and the round sizes into device memory.
+int stage_round(hetm_ctx *c, const hetm_log_entry *log, uint64_t n_log) {
+    auto &st = c->stage[c->stage_cur];
+    CK(cudaEventSynchronize(st.used));
+    const uint32_t nb = (uint32_t)c->pending.size();
+    uint64_t total = 0;
+    for (uint32_t b = 0; b < nb; ++b) {
+        st.batches[b] = c->pending[b];
+        st.prefix[b] = total;
+        st.rounds[1 + b] = DevRound{c->pending[b].n_tx, 0, nullptr, 1, 0};
+        total += c->pending[b].n_tx;
+    }
+    st.prefix[nb] = total;
+    st.rounds[0] = DevRound{total, n_log, log, nb, 0};
+    CK(cudaMemcpyAsync(c->d_round, st.rounds, sizeof(DevRound) * (1 + nb), cudaMemcpyHostToDevice,
+                       c->stream));
+    if (nb) {
+        CK(cudaMemcpyAsync(c->d_batches, st.batches, sizeof(DevBatch) * nb, cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_prefix, st.prefix, sizeof(uint64_t) * (nb + 1),
+                           cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(cudaEventRecord(st.used, c->stream));
+    c->stage_cur ^= 1;
+    return HETM_OK;
+}
+
+ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
+                   const uint64_t *prefix) {
+    ExecArgs a{};
+    a.W = c->W;
+    a.n_words = c->n_words;
+    a.locks = c->locks;
+    a.lock_mask = (1u << c->cfg.lock_log2) - 1;
+    a.lock_shift = c->cfg.lock_shift;
+    a.gv = &c->scr->gv;
+    a.rs = c->rs;
+    a.gshift = c->gshift;
+    a.ws = c->ws;
+    a.cshift = c->cshift;
+    a.rp = rp;
+    a.batches = batches;
+    a.prefix = prefix;
+    a.next = &c->scr->next;
+    a.max_attempts = c->cfg.max_attempts;
+    a.budget_ns = 20ull * 1000 * 1000 * 1000;
+    a.counters = c->scr->counters;
+    a.err = &c->scr->err;
+    a.cache_log2_sets = c->cfg.cache_log2_sets;
+    a.key_base = c->cfg.cache_key_base;
+    a.val_base = c->cfg.cache_val_base;
+    a.lru_base = c->cfg.cache_lru_base;
+    a.ver_base = c->cfg.cache_ver_base;
+    return a;
+}
+
+// Executor launch(es) for the staged table: one persistent launch over all
+// batches, or one launch per batch.
+int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb) {
+    if (!per_batch) {
+        CK(cudaMemsetAsync(&c->scr->next, 0, sizeof(unsigned long long), c->stream));
+        CK(launch_exec(exec_args(c, c->d_round, c->d_batches, c->d_prefix), c->exec_blocks,
+                       c->exec_threads, c->stream));
+        return HETM_OK;
+    }
+    for (uint32_t b = 0; b < nb; ++b) {
+        CK(cudaMemsetAsync(&c->scr->next, 0, sizeof(unsigned long long), c->stream));
+        CK(launch_exec(exec_args(c, c->d_round + 1 + b, c->d_batches + b, c->d_prefix0),
+                       c->exec_blocks, c->exec_threads, c->stream));
+    }
+    return HETM_OK;
+}
+
+// validate (+ TS max) -> apply -> merge -> clear; events e[0..3] between
+// phases when non-null.
+int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e) {
+    CK(cudaMemsetAsync(&c->scr->conflicts, 0, 2 * sizeof(unsigned long long), c->stream));
+    if (e) CK(cudaEventRecordWithFlags(e[0], c->stream, cudaEventRecordExternal));
+    CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, flags, &c->scr->conflicts, c->TS,
+                       &c->scr->err, c->stream_blocks, c->stream));
+    if (e) CK(cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
+    CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream));
+    if (e) CK(cudaEventRecordWithFlags(e[2], c->stream, cudaEventRecordExternal));
+    CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, force,
+                    &c->scr->dirty, c->stream_blocks, c->stream));
+    CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
+    CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
+    if (e) CK(cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal));
+    CK(cudaMemcpyAsync(c->out, c->scr->counters, sizeof(RoundOut) - sizeof(int) * 2,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&c->out->err, &c->scr->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    return HETM_OK;
+}
+
+int capture(hetm_ctx *c, cudaGraphExec_t *out, int which) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = which == 0 ? enqueue_exec(c, false, 0) : enqueue_sync(c, nullptr, -1, c->ev + 1);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc != HETM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    CK(e);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return HETM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hetm_strerror(int code) {
+    switch (code) {
+        case HETM_OK: return "ok";
+        case HETM_EINVAL: return "invalid argument or precondition violated";
+        case HETM_ENOMEM: return "out of device or pinned host memory";
+        case HETM_ECAPACITY: return "fixed-capacity buffer or table full";
+        case HETM_ETIMEOUT: return "bounded device wait gave up";
+        case HETM_ECUDA: return "CUDA runtime error";
+        case HETM_EBUSY: return "not admitted now; retry later";
+        case HETM_EDEVICE: return "kernel met an out-of-range address";
+        default: return "unknown error";
+    }
+}
+
+int hetm_config_default(hetm_config *cfg) {
+    if (!cfg) return HETM_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->ws_chunk_bytes = 16384;
+    cfg->lock_log2 = 22;
+    cfg->lock_shift = 0;
+    cfg->exec_blocks = 0;
+    cfg->exec_threads = 256;
+    cfg->max_attempts = 1u << 16;
+    cfg->cpu_threads = 8;
+    cfg->log_chunk_bytes = 49152;
+    cfg->log_capacity = 1ull << 24;
+    cfg->cpu_log_capacity = 1ull << 21;
+    cfg->max_batches = 4096;
+    return HETM_OK;
+}
+
+void hetm_destroy(hetm_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->ship) cudaStreamSynchronize(c->ship);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->g_exec) cudaGraphExecDestroy(c->g_exec);
+    if (c->g_sync) cudaGraphExecDestroy(c->g_sync);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &s : c->stage) {
+        if (s.rounds) cudaFreeHost(s.rounds);
+        if (s.batches) cudaFreeHost(s.batches);
+        if (s.prefix) cudaFreeHost(s.prefix);
+        if (s.used) cudaEventDestroy(s.used);
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (c->dlog_free[i]) cudaEventDestroy(c->dlog_free[i]);
+        if (c->tlog_free[i]) cudaEventDestroy(c->tlog_free[i]);
+    }
+    if (c->ship_done) cudaEventDestroy(c->ship_done);
+    for (auto &L : c->tlogs)
+        for (auto *b : L->buf)
+            if (b) cudaFreeHost(b);
+    if (c->out) cudaFreeHost(c->out);
+    for (void *p : c->dev_allocs) {
+        if (c->cfg.dev_free) c->cfg.dev_free(p, c->cfg.alloc_user);
+        else cudaFree(p);
+    }
+    if (c->ship) cudaStreamDestroy(c->ship);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const hetm_config *cfg,
+              void *stream) {
+    if (!out || stmr_words == 0 || stmr_words >= (1ull << 32)) return HETM_EINVAL;
+    if (!pow2(granule_bytes) || granule_bytes < 4) return HETM_EINVAL;
+    hetm_config d;
+    hetm_config_default(&d);
+    if (cfg) d = *cfg;
+    if (!pow2(d.ws_chunk_bytes) || d.ws_chunk_bytes < 16) return HETM_EINVAL;
+    if (d.lock_log2 < 1 || d.lock_log2 > 30 || d.lock_shift > 31) return HETM_EINVAL;
+    if (d.exec_threads == 0 || d.exec_threads % 32 || d.exec_threads > 256) return HETM_EINVAL;
+    if (d.log_chunk_bytes < 12 || d.log_chunk_bytes % 12 || d.max_attempts == 0) return HETM_EINVAL;
+    if (d.max_batches == 0 || d.cpu_threads == 0 || d.log_capacity == 0) return HETM_EINVAL;
+    if (d.cache_log2_sets > 28) return HETM_EINVAL;
+
+    hetm_ctx *c = new (std::nothrow) hetm_ctx();
+    if (!c) return HETM_ENOMEM;
+    c->cfg = d;
+    c->n_words = stmr_words;
+    c->granule_bytes = granule_bytes;
+    c->gshift = (uint32_t)ilog2(granule_bytes / 4);
+    c->cshift = (uint32_t)ilog2(d.ws_chunk_bytes / 4);
+    const uint64_t n_gran = ((stmr_words - 1) >> c->gshift) + 1;
+    const uint64_t n_chunk = ((stmr_words - 1) >> c->cshift) + 1;
+    c->rs_words = (n_gran + 31) / 32;
+    c->ws_words = (n_chunk + 31) / 32;
+
+    auto fail = [&](int rc) {
+        hetm_destroy(c);
+        return rc;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return fail(HETM_ECUDA);
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return fail(HETM_ECUDA);
+    if (stream) {
+        c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(HETM_ECUDA);
+        c->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&c->ship, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(HETM_ECUDA);
+
+    const uint32_t nb = d.max_batches;
+    if (!dev_alloc_t(c, &c->W, stmr_words) || !dev_alloc_t(c, &c->S, stmr_words) ||
+        !dev_alloc_t(c, &c->TS, stmr_words) || !dev_alloc_t(c, &c->rs, c->rs_words) ||
+        !dev_alloc_t(c, &c->ws, c->ws_words) || !dev_alloc_t(c, &c->locks, 1ull << d.lock_log2) ||
+        !dev_alloc_t(c, &c->scr, 1) || !dev_alloc_t(c, &c->d_round, nb + 1) ||
+        !dev_alloc_t(c, &c->d_batches, nb) || !dev_alloc_t(c, &c->d_prefix, nb + 1) ||
+        !dev_alloc_t(c, &c->d_prefix0, 2) || !dev_alloc_t(c, &c->dlog[0], d.log_capacity) ||
+        !dev_alloc_t(c, &c->dlog[1], d.log_capacity))
+        return fail(HETM_ENOMEM);
+    for (auto &s : c->stage) {
+        if (!host_alloc_t(&s.rounds, nb + 1) || !host_alloc_t(&s.batches, nb) ||
+            !host_alloc_t(&s.prefix, nb + 1))
+            return fail(HETM_ENOMEM);
+        if (cudaEventCreateWithFlags(&s.used, cudaEventDisableTiming) != cudaSuccess)
+            return fail(HETM_ECUDA);
+    }
+    if (!host_alloc_t(&c->out, 1)) return fail(HETM_ENOMEM);
+    std::memset(c->out, 0, sizeof(RoundOut));
+    for (int i = 0; i < 2; ++i) {
+        if (cudaEventCreateWithFlags(&c->dlog_free[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->tlog_free[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(HETM_ECUDA);
+    }
+    if (cudaEventCreateWithFlags(&c->ship_done, cudaEventDisableTiming) != cudaSuccess)
+        return fail(HETM_ECUDA);
+    for (auto &e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(HETM_ECUDA);
+    for (uint32_t t = 0; t < d.cpu_threads; ++t) c->tlogs.emplace_back(new ThreadLog());
+
+    int occ = 0;
+    c->exec_threads = (int)d.exec_threads;
+    if (exec_occupancy(c->exec_threads, &occ) != 0 || occ < 1) occ = 1;
+    c->exec_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ;
+    c->stream_blocks = c->n_sm * 8;
+
+    if (cudaMemsetAsync(c->locks, 0, (1ull << d.lock_log2) * 8, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->scr, 0, sizeof(Scratch), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_prefix0, 0, 16, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->TS, 0, stmr_words * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->W, 0, stmr_words * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->S, 0, stmr_words * 4, c->stream) != cudaSuccess)
+        return fail(HETM_ECUDA);
+    for (int i = 0; i < 2; ++i) {
+        if (cudaEventRecord(c->dlog_free[i], c->stream) != cudaSuccess ||
+            cudaEventRecord(c->tlog_free[i], c->ship) != cudaSuccess ||
+            cudaEventRecord(c->stage[i].used, c->stream) != cudaSuccess)
+            return fail(HETM_ECUDA);
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(HETM_ECUDA);
+    *out = c;
+    return HETM_OK;
+}
+
+int hetm_load(hetm_ctx *c, const int32_t *src, uint64_t n) {
+    if (!c || !src || n != c->n_words) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->ship));
+    CK(cudaMemcpyAsync(c->W, src, n * 4, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(c->S, c->W, n * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(c->TS, 0, n * 4, c->stream));
+    CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
+    CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
+    CK(cudaMemsetAsync(c->locks, 0, (1ull << c->cfg.lock_log2) * 8, c->stream));
+    CK(cudaMemsetAsync(c->scr, 0, sizeof(Scratch), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto &L : c->tlogs) {
+        std::lock_guard<std::mutex> g(L->mu);
+        L->fill = L->shipped = 0;
+    }
+    c->dlog_fill.store(0);
+    c->pending.clear();
+    c->attached = nullptr;
+    c->attached_n = 0;
+    std::memset(c->prev_counters, 0, sizeof(c->prev_counters));
+    return HETM_OK;
+}
+
+int hetm_read_stmr(hetm_ctx *c, int which, int32_t *dst, uint64_t off, uint64_t n) {
+    if (!c || !dst || (which != 0 && which != 1) || off > c->n_words || n > c->n_words - off)
+        return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(dst, (which ? c->S : c->W) + off, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HETM_OK;
+}
+
+void *hetm_device_ptr(hetm_ctx *c, int which) {
+    if (!c) return nullptr;
+    switch (which) {
+        case 0: return c->W;
+        case 1: return c->S;
+        case 2: return c->TS;
+        case 3: return c->rs;
+        case 4: return c->ws;
+        default: return nullptr;
+    }
+}
+
+int hetm_bitmap_words(hetm_ctx *c, uint64_t *rs_words, uint64_t *ws_words) {
+    if (!c) return HETM_EINVAL;
+    if (rs_words) *rs_words = c->rs_words;
+    if (ws_words) *ws_words = c->ws_words;
+    return HETM_OK;
+}
+
+int hetm_sync(hetm_ctx *c) {
+    if (!c) return HETM_EINVAL;
+    CK(cudaStreamSynchronize(c->ship));
+    CK(cudaStreamSynchronize(c->stream));
+    return HETM_OK;
+}
+
+int hetm_gpu_submit_batch(hetm_ctx *c, const hetm_batch *b, uint64_t *batch_id) {
+    if (!c || !b) return HETM_EINVAL;
+    if (b->workload < HETM_WL_BANK || b->workload > HETM_WL_CACHE) return HETM_EINVAL;
+    if (b->n_tx && !b->tx) return HETM_EINVAL;
+    if (b->workload == HETM_WL_CACHE) {
+        const hetm_config &f = c->cfg;
+        const uint64_t ns = 1ull << f.cache_log2_sets;
+        // one lock stripe per set region: needs >= 16-word stripes, aligned regions
+        if (f.lock_shift < 4 || f.cache_key_base % 16 || f.cache_val_base % 16 ||
+            f.cache_lru_base % 16 || f.cache_key_base + 16 * ns > c->n_words ||
+            f.cache_val_base + 16 * ns > c->n_words || f.cache_lru_base + 8 * ns > c->n_words ||
+            f.cache_ver_base + ns > c->n_words)
+            return HETM_EINVAL;
+    }
+    if (c->pending.size() >= c->cfg.max_batches) return HETM_EBUSY;
+    DevBatch d{b->workload, b->n_tx, b->tx, b->order, b->status, b->out, b->txid_base, b->word_base};
+    c->pending.push_back(d);
+    if (batch_id) *batch_id = c->next_batch_id++;
+    return HETM_OK;
+}
+
+int hetm_gpu_exec(hetm_ctx *c, int per_batch) {
+    if (!c) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    if (c->pending.empty()) return HETM_OK;
+    int rc = stage_round(c, nullptr, 0);
+    if (rc != HETM_OK) return rc;
+    rc = enqueue_exec(c, per_batch != 0, (uint32_t)c->pending.size());
+    c->pending.clear();
+    return rc;
+}
+
+int hetm_exec_counters(hetm_ctx *c, uint64_t *committed, uint64_t *gave_up, uint64_t *aborts) {
+    if (!c) return HETM_EINVAL;
+    unsigned long long h[3];
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(h, c->scr->counters, sizeof(h), cudaMemcpyDeviceToHost));
+    if (committed) *committed = h[0];
+    if (gave_up) *gave_up = h[1];
+    if (aborts) *aborts = h[2];
+    int err = 0;
+    CK(cudaMemcpy(&err, &c->scr->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err == kErrTimeout) return HETM_ETIMEOUT;
+    return err ? HETM_EDEVICE : HETM_OK;
+}
+
+int hetm_gpu_mark(hetm_ctx *c, const uint32_t *addr, const int32_t *vals, uint64_t n) {
+    if (!c || (n && !addr)) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(launch_mark(addr, vals, n, c->W, c->n_words, c->rs, c->gshift, c->ws, c->cshift,
+                   &c->scr->err, c->n_sm * 4, c->stream));
+    return HETM_OK;
+}
+
+int hetm_cpu_log_write(hetm_ctx *c, uint32_t thread, const hetm_log_entry *e, uint32_t n) {
+    if (!c || thread >= c->tlogs.size() || (n && !e)) return HETM_EINVAL;
+    ThreadLog &L = *c->tlogs[thread];
+    std::lock_guard<std::mutex> g(L.mu);
+    if (!L.buf[L.cur]) {
+        if (cudaSetDevice(c->device) != cudaSuccess) return HETM_ECUDA;
+        if (!host_alloc_t(&L.buf[0], c->cfg.cpu_log_capacity) ||
+            !host_alloc_t(&L.buf[1], c->cfg.cpu_log_capacity))
+            return HETM_ENOMEM;
+    }
+    if (L.fill + n > c->cfg.cpu_log_capacity) return HETM_ECAPACITY;
+    std::memcpy(L.buf[L.cur] + L.fill, e, (size_t)n * sizeof(hetm_log_entry));
+    L.fill += n;
+    const uint64_t chunk = c->cfg.log_chunk_bytes / sizeof(hetm_log_entry);
+    while (L.fill - L.shipped >= chunk) {
+        int rc = ship_locked(c, L, chunk);
+        if (rc != HETM_OK) return rc;
+    }
+    return HETM_OK;
+}
+
+int hetm_log_attach(hetm_ctx *c, const hetm_log_entry *dev_log, uint64_t n) {
+    if (!c || (n && !dev_log) || (reinterpret_cast<uintptr_t>(dev_log) & 15)) return HETM_EINVAL;
+    c->attached = dev_log;
+    c->attached_n = n;
+    return HETM_OK;
+}
+
+int hetm_validate(hetm_ctx *c, uint64_t *n_conflicts, uint32_t *dev_flag_bits) {
+    if (!c) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    const hetm_log_entry *log = nullptr;
+    uint64_t n = 0;
+    int rc = flush_logs(c, &log, &n);
+    if (rc != HETM_OK) return rc;
+    std::vector<DevBatch> keep;
+    keep.swap(c->pending);  // the table is staged by the exec call, not here
+    rc = stage_round(c, log, n);
+    keep.swap(c->pending);
+    if (rc != HETM_OK) return rc;
+    CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
+    CK(cudaMemsetAsync(&c->scr->conflicts, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, dev_flag_bits, &c->scr->conflicts,
+                       c->TS, &c->scr->err, c->stream_blocks, c->stream));
+    CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream));
+    CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
+    if (n_conflicts) {
+        unsigned long long h = 0;
+        int err = 0;
+        CK(cudaMemcpyAsync(&c->out->conflicts, &c->scr->conflicts, 8, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaMemcpyAsync(&c->out->err, &c->scr->err, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        h = c->out->conflicts;
+        err = c->out->err;
+        *n_conflicts = h;
+        if (err) return err == kErrTimeout ? HETM_ETIMEOUT : HETM_EDEVICE;
+    }
+    return HETM_OK;
+}
+
+int hetm_validate_only(hetm_ctx *c, const hetm_log_entry *dev_log, uint64_t n,
+                       uint32_t *dev_flag_bits, uint64_t *dev_count) {
+    if (!c || (n && !dev_log) || (reinterpret_cast<uintptr_t>(dev_log) & 15)) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    if (n == 0) return HETM_OK;
+    CK(launch_validate_direct(dev_log, n, c->rs, c->gshift, c->n_words, dev_flag_bits,
+                              reinterpret_cast<unsigned long long *>(dev_count), &c->scr->err,
+                              c->stream_blocks, c->stream));
+    return HETM_OK;
+}
+
+int hetm_merge(hetm_ctx *c, int conflict) {
+    if (!c || conflict < -1 || conflict > 1) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemsetAsync(&c->scr->dirty, 0, sizeof(unsigned long long), c->stream));
+    CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, conflict,
+                    &c->scr->dirty, c->stream_blocks, c->stream));
+    CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
+    CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
+    return HETM_OK;
+}
+
+int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
+    if (!c) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    if (!c->g_exec) {
+        int rc = capture(c, &c->g_exec, 0);
+        if (rc != HETM_OK) return rc;
+    }
+    if (!c->g_sync) {
+        int rc = capture(c, &c->g_sync, 1);
+        if (rc != HETM_OK) return rc;
+    }
+    const uint32_t nb = (uint32_t)c->pending.size();
+    // the executor starts right away; log chunks keep shipping meanwhile
+    int rc = stage_round(c, nullptr, 0);
+    if (rc != HETM_OK) return rc;
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    if (nb) CK(cudaGraphLaunch(c->g_exec, c->stream));
+    CK(cudaEventRecord(c->ev[6], c->stream));
+    c->pending.clear();
+    // end of the execution phase: ship the rest of the logs, then validate
+    const hetm_log_entry *log = nullptr;
+    uint64_t n = 0;
+    rc = flush_logs(c, &log, &n);
+    if (rc != HETM_OK) return rc;
+    rc = stage_round(c, log, n);
+    if (rc != HETM_OK) return rc;
+    CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
+    CK(cudaGraphLaunch(c->g_sync, c->stream));
+    CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
+    CK(cudaEventRecord(c->ev[5], c->stream));
+    if (!stats) return HETM_OK;
+    CK(cudaEventSynchronize(c->ev[5]));
+    std::memset(stats, 0, sizeof(*stats));
+    stats->n_log = n;
+    stats->n_conflicts = c->out->conflicts;
+    stats->conflict = c->out->conflicts != 0;
+    stats->err = c->out->err == 0 ? HETM_OK : (c->out->err == kErrTimeout ? HETM_ETIMEOUT : HETM_EDEVICE);
+    stats->committed = c->out->counters[0] - c->prev_counters[0];
+    stats->gave_up = c->out->counters[1] - c->prev_counters[1];
+    stats->aborts = c->out->counters[2] - c->prev_counters[2];
+    std::memcpy(c->prev_counters, c->out->counters, sizeof(c->prev_counters));
+    stats->dirty_chunks = c->out->dirty;
+    stats->n_batches = nb;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[6]) == cudaSuccess) stats->ms_exec = ms;
+    if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) stats->ms_validate = ms;
+    if (cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]) == cudaSuccess) stats->ms_apply = ms;
+    if (cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]) == cudaSuccess) stats->ms_merge = ms;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]) == cudaSuccess) stats->ms_total = ms;
+    return stats->err;
+}
+
+}  // extern "C"

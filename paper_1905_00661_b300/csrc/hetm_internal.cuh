@@ -1,0 +1,142 @@
+// Internal declarations of the SHeTM round library (CUDA, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hetm.h"
+
+namespace hetm {
+
+constexpr uint8_t kCommitted = 1;
+constexpr uint8_t kGaveUp = 2;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Device-side batch descriptor (one per admitted batch).
+struct DevBatch {
+    uint32_t workload;
+    uint32_t n_tx;
+    const void *tx;
+    uint64_t *order;
+    uint8_t *status;
+    void *out;
+    uint32_t txid_base;
+    uint32_t word_base;
+};
+
+// Per-round sizes, read by the kernels from device memory so that one
+// captured graph serves every round.
+struct DevRound {
+    uint64_t total_tx;            // transactions over all batches
+    uint64_t n_log;               // CPU tuples to validate
+    const hetm_log_entry *log;    // device log of this round
+    uint32_t n_batches;
+    uint32_t pad;
+};
+
+// Device error word values (first error wins).
+constexpr int kErrAddr = 1;
+constexpr int kErrTimeout = 2;
+
+// Arguments of the executor kernel.
+struct ExecArgs {
+    int32_t *W;
+    uint64_t n_words;
+    unsigned long long *locks;
+    uint32_t lock_mask;
+    uint32_t lock_shift;
+    unsigned long long *gv;        // global commit-version clock
+    uint32_t *rs;                  // RS_bmp
+    uint32_t gshift;               // granule(a) = a >> gshift
+    uint32_t *ws;                  // WS_bmp
+    uint32_t cshift;               // chunk(a) = a >> cshift
+    const DevRound *rp;
+    const DevBatch *batches;
+    const uint64_t *prefix;        // n_batches + 1 prefix sums of n_tx
+    unsigned long long *next;      // work counter (reset per launch)
+    uint32_t max_attempts;
+    unsigned long long budget_ns;  // wall-clock bound of one launch
+    unsigned long long *counters;  // [0] committed [1] gave up [2] aborts
+    int *err;
+    uint32_t cache_log2_sets;
+    uint64_t key_base, val_base, lru_base, ver_base;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned long long ld_rlx64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int32_t ld_rlx32(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t ld_rlx_u64(const int32_t *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rlx32(int32_t *p, int32_t v) {
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_rlx_u64w(int32_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rlx64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// streaming 16-byte load that does not allocate in L1
+__device__ __forceinline__ uint4 ld_stream16(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void set_err(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// SplitMix64 finalizer (Steele, Lea & Flood 2014): the cache's set hash.
+__device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ----------------------------------------------------------- host launchers
+cudaError_t launch_exec(const ExecArgs &a, int blocks, int threads, cudaStream_t s);
+int exec_occupancy(int threads, int *blocks_per_sm);
+
+cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
+                            uint64_t n_words, uint32_t *flags, unsigned long long *count,
+                            uint32_t *ts, int *err, int blocks, cudaStream_t s);
+cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const uint32_t *rs,
+                                   uint32_t gshift, uint64_t n_words, uint32_t *flags,
+                                   unsigned long long *count, int *err, int blocks, cudaStream_t s);
+cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int32_t *S,
+                         uint64_t n_words, int blocks, cudaStream_t s);
+cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_t *S,
+                         uint64_t n_words, const unsigned long long *conflicts, int force,
+                         unsigned long long *dirty_count, int blocks, cudaStream_t s);
+cudaError_t launch_mark(const uint32_t *addr, const int32_t *vals, uint64_t n, int32_t *W,
+                        uint64_t n_words, uint32_t *rs, uint32_t gshift, uint32_t *ws,
+                        uint32_t cshift, int *err, int blocks, cudaStream_t s);
+
+}  // namespace hetm

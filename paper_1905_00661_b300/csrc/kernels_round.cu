@@ -1,0 +1,284 @@
+// Validation, apply and merge kernels of a SHeTM round (Sec. IV-C, IV-D).
+//
+// All three stream an HBM-resident array once: the CPU write-set log (12-byte
+// tuples) for validate/apply, STMR^W and STMR^S on the dirty chunks for the
+// merge.  Loads are 16-byte vectors, non-allocating in L1, and every warp
+// keeps the next tile's loads in flight while it works on the current one.
+
+#include "hetm_internal.cuh"
+
+namespace hetm {
+namespace {
+
+// A warp tile is 128 log tuples = 1536 B: lane l owns tuples 4l..4l+3, read
+// as three 16-byte vectors.  Tuple j of the lane sits in these vector words:
+//   addr  q0.x q0.w q1.z q2.y
+//   value q0.y q1.x q1.w q2.z
+//   ts    q0.z q1.y q2.x q2.w
+struct Tile {
+    uint4 q0, q1, q2;
+};
+
+__device__ __forceinline__ Tile load_tile(const hetm_log_entry *log, uint64_t tile, unsigned lane) {
+    const char *p = reinterpret_cast<const char *>(log) + tile * 1536ull + lane * 48u;
+    Tile t;
+    t.q0 = ld_stream16(p);
+    t.q1 = ld_stream16(p + 16);
+    t.q2 = ld_stream16(p + 32);
+    return t;
+}
+
+__device__ __forceinline__ void tile_fields(const Tile &t, uint32_t a[4], int32_t v[4], uint32_t s[4]) {
+    a[0] = t.q0.x; a[1] = t.q0.w; a[2] = t.q1.z; a[3] = t.q2.y;
+    v[0] = (int32_t)t.q0.y; v[1] = (int32_t)t.q1.x; v[2] = (int32_t)t.q1.w; v[3] = (int32_t)t.q2.z;
+    s[0] = t.q0.z; s[1] = t.q1.y; s[2] = t.q2.x; s[3] = t.q2.w;
+}
+
+__device__ __forceinline__ uint32_t rs_bit(const uint32_t *rs, uint32_t a, uint32_t gshift) {
+    uint32_t g = a >> gshift;
+    return (__ldg(rs + (g >> 5)) >> (g & 31)) & 1u;
+}
+
+// Validation (Sec. IV-C): flag = RS_bmp[granule(addr)] for every tuple, the
+// flags bit-packed in log order, the hits counted.  kMax additionally raises
+// TS[addr] to the tuple's timestamp (first pass of the apply).
+template <bool kMax>
+__device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__ log, uint64_t n,
+                                              const uint32_t *__restrict__ rs, uint32_t gshift,
+                                              uint64_t n_words, uint32_t *__restrict__ flags,
+                                              unsigned long long *count, uint32_t *ts, int *err) {
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = (gridDim.x * (uint64_t)blockDim.x) >> 5;
+    const uint64_t n_tiles = n / 128;
+    uint32_t hits = 0;
+    bool bad = false;
+
+    uint64_t c = warp;
+    Tile next;
+    if (c < n_tiles) next = load_tile(log, c, lane);
+    for (; c < n_tiles; c += n_warps) {
+        Tile cur = next;
+        if (c + n_warps < n_tiles) next = load_tile(log, c + n_warps, lane);
+        uint32_t a[4], s[4];
+        int32_t v[4];
+        tile_fields(cur, a, v, s);
+        uint32_t nib = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (a[j] < n_words) {
+                nib |= rs_bit(rs, a[j], gshift) << j;
+                if (kMax) atomicMax(ts + a[j], s[j]);
+            } else {
+                bad = true;
+            }
+        }
+        hits += __popc(nib);
+        // flag word k of the tile covers tuples 32k..32k+31 = lanes 8k..8k+7
+        uint32_t w = nib << (4u * (lane & 7u));
+        w |= __shfl_xor_sync(kFull, w, 1);
+        w |= __shfl_xor_sync(kFull, w, 2);
+        w |= __shfl_xor_sync(kFull, w, 4);
+        if (flags && (lane & 7u) == 0) flags[c * 4 + (lane >> 3)] = w;
+    }
+    // ragged tail (< 128 tuples): one warp, one tuple per lane per step
+    if (warp == n_warps - 1) {
+        for (uint64_t e0 = n_tiles * 128; e0 < n; e0 += 32) {
+            uint64_t i = e0 + lane;
+            uint32_t bit = 0;
+            if (i < n) {
+                uint32_t a = log[i].addr;
+                if (a < n_words) {
+                    bit = rs_bit(rs, a, gshift);
+                    if (kMax) atomicMax(ts + a, log[i].ts);
+                } else {
+                    bad = true;
+                }
+            }
+            uint32_t w = __ballot_sync(kFull, bit);
+            hits += bit;
+            if (flags && lane == 0) flags[e0 / 32] = w;
+        }
+    }
+    if (bad) set_err(err, kErrAddr);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(kFull, hits, o);
+    if (lane == 0 && hits && count) atomicAdd(count, (unsigned long long)hits);
+}
+
+template <bool kMax>
+__global__ void __launch_bounds__(256) k_validate_round(const DevRound *rp, const uint32_t *rs,
+                                                        uint32_t gshift, uint64_t n_words,
+                                                        uint32_t *flags, unsigned long long *count,
+                                                        uint32_t *ts, int *err) {
+    validate_body<kMax>(rp->log, rp->n_log, rs, gshift, n_words, flags, count, ts, err);
+}
+
+__global__ void __launch_bounds__(256) k_validate_direct(const hetm_log_entry *log, uint64_t n,
+                                                         const uint32_t *rs, uint32_t gshift,
+                                                         uint64_t n_words, uint32_t *flags,
+                                                         unsigned long long *count, int *err) {
+    validate_body<false>(log, n, rs, gshift, n_words, flags, count, nullptr, err);
+}
+
+// Apply, second pass (Sec. IV-C): after TS holds the newest timestamp of
+// every logged word, exactly the tuple carrying it writes its value into
+// STMR^W and into the shadow STMR^S (Sec. IV-D: the shadow plus the CPU log
+// is the CPU's state).  Out-of-range tuples were reported by validation.
+__global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_t *__restrict__ ts,
+                                               int32_t *__restrict__ W, int32_t *__restrict__ S,
+                                               uint64_t n_words) {
+    const hetm_log_entry *log = rp->log;
+    const uint64_t n = rp->n_log;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = (gridDim.x * (uint64_t)blockDim.x) >> 5;
+    const uint64_t n_tiles = n / 128;
+    uint64_t c = warp;
+    Tile next;
+    if (c < n_tiles) next = load_tile(log, c, lane);
+    for (; c < n_tiles; c += n_warps) {
+        Tile cur = next;
+        if (c + n_warps < n_tiles) next = load_tile(log, c + n_warps, lane);
+        uint32_t a[4], s[4];
+        int32_t v[4];
+        tile_fields(cur, a, v, s);
+        uint32_t t[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[j] = a[j] < n_words ? __ldcg(ts + a[j]) : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (a[j] < n_words && t[j] == s[j]) {
+                W[a[j]] = v[j];
+                S[a[j]] = v[j];
+            }
+        }
+    }
+    if (warp == n_warps - 1) {
+        for (uint64_t i = n_tiles * 128 + lane; i < n; i += 32) {
+            uint32_t a = log[i].addr;
+            if (a < n_words && __ldcg(ts + a) == log[i].ts) {
+                W[a] = log[i].value;
+                S[a] = log[i].value;
+            }
+        }
+    }
+}
+
+// Merge (Sec. IV-C Merge Phase, Sec. IV-D): every WS_bmp chunk is copied
+// W -> S when validation succeeded (the GPU's speculative commits become
+// final) or S -> W when it failed (the GPU batch is undone; S already holds
+// start + CPU writes).  A warp moves 2 KiB per step, 4 vectors per lane.
+__global__ void __launch_bounds__(256) k_merge(const uint32_t *__restrict__ ws, uint32_t cshift,
+                                               int32_t *W, int32_t *S, uint64_t n_words,
+                                               const unsigned long long *conflicts, int force,
+                                               unsigned long long *dirty_count) {
+    const bool conflict = force >= 0 ? force != 0 : (*conflicts != 0ull);
+    const uint4 *src = reinterpret_cast<const uint4 *>(conflict ? S : W);
+    uint4 *dst = reinterpret_cast<uint4 *>(conflict ? W : S);
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t n_threads = gridDim.x * (uint64_t)blockDim.x;
+    const uint64_t warp = tid >> 5, n_warps = n_threads >> 5;
+    const uint64_t n_vec = n_words / 4;
+    const uint64_t n_spans = (n_vec + 127) / 128;
+    for (uint64_t sp = warp; sp < n_spans; sp += n_warps) {
+        uint4 r[4];
+        bool d[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint64_t v = sp * 128 + lane + 32u * k;
+            uint64_t ch = (v * 4) >> cshift;
+            d[k] = v < n_vec && ((__ldg(ws + (ch >> 5)) >> (ch & 31)) & 1u);
+            if (d[k]) r[k] = __ldcs(src + v);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (d[k]) __stcs(dst + sp * 128 + lane + 32u * k, r[k]);
+    }
+    // the last n_words % 4 words
+    if (tid == 0) {
+        for (uint64_t w = n_vec * 4; w < n_words; ++w) {
+            uint64_t ch = w >> cshift;
+            if ((ws[ch >> 5] >> (ch & 31)) & 1u) {
+                int32_t *d = conflict ? W : S;
+                const int32_t *s = conflict ? S : W;
+                d[w] = s[w];
+            }
+        }
+    }
+    if (dirty_count) {
+        const uint64_t n_chunks = ((n_words - 1) >> cshift) + 1;
+        const uint64_t n_ws = (n_chunks + 31) / 32;
+        unsigned long long c = 0;
+        for (uint64_t i = tid; i < n_ws; i += n_threads) c += __popc(ws[i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0 && c) atomicAdd(dirty_count, c);
+    }
+}
+
+// Planted GPU accesses: non-transactional writes (or reads, vals == NULL)
+// recorded in RS_bmp, and writes also in WS_bmp, as a committing GPU
+// transaction would (Sec. IV-B, IV-C).
+__global__ void k_mark(const uint32_t *__restrict__ addr, const int32_t *__restrict__ vals,
+                       uint64_t n, int32_t *W, uint64_t n_words, uint32_t *rs, uint32_t gshift,
+                       uint32_t *ws, uint32_t cshift, int *err) {
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t a = addr[i];
+        if (a >= n_words) {
+            set_err(err, kErrAddr);
+            continue;
+        }
+        uint32_t g = a >> gshift;
+        atomicOr(rs + (g >> 5), 1u << (g & 31));
+        if (vals) {
+            W[a] = vals[i];
+            uint32_t ch = a >> cshift;
+            atomicOr(ws + (ch >> 5), 1u << (ch & 31));
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
+                            uint64_t n_words, uint32_t *flags, unsigned long long *count,
+                            uint32_t *ts, int *err, int blocks, cudaStream_t s) {
+    if (ts)
+        k_validate_round<true><<<blocks, 256, 0, s>>>(rp, rs, gshift, n_words, flags, count, ts, err);
+    else
+        k_validate_round<false><<<blocks, 256, 0, s>>>(rp, rs, gshift, n_words, flags, count, ts, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const uint32_t *rs,
+                                   uint32_t gshift, uint64_t n_words, uint32_t *flags,
+                                   unsigned long long *count, int *err, int blocks, cudaStream_t s) {
+    k_validate_direct<<<blocks, 256, 0, s>>>(log, n, rs, gshift, n_words, flags, count, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int32_t *S,
+                         uint64_t n_words, int blocks, cudaStream_t s) {
+    k_apply<<<blocks, 256, 0, s>>>(rp, ts, W, S, n_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_t *S,
+                         uint64_t n_words, const unsigned long long *conflicts, int force,
+                         unsigned long long *dirty_count, int blocks, cudaStream_t s) {
+    k_merge<<<blocks, 256, 0, s>>>(ws, cshift, W, S, n_words, conflicts, force, dirty_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark(const uint32_t *addr, const int32_t *vals, uint64_t n, int32_t *W,
+                        uint64_t n_words, uint32_t *rs, uint32_t gshift, uint32_t *ws,
+                        uint32_t cshift, int *err, int blocks, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_mark<<<blocks, 256, 0, s>>>(addr, vals, n, W, n_words, rs, gshift, ws, cshift, err);
+    return cudaGetLastError();
+}
+
+}  // namespace hetm

@@ -1,0 +1,54 @@
+"""The C-ABI library loads and exports every symbol include/hetm.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hetm.h")).read()
+    return set(re.findall(r"HETM_API[^;(]*?\b(hetm_\w+)\s*\(", src))
+
+
+def test_header_declares_binding_symbols():
+    import paper_1905_00661_b300 as h
+    assert _declared() == set(h.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1905_00661_b300 as h
+    L = ctypes.CDLL(h.LIB_PATH)
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_strerror_and_defaults_without_gpu():
+    import paper_1905_00661_b300 as h
+    assert h.strerror(h.HETM_OK) == "ok"
+    assert "capacity" in h.strerror(h.HETM_ECAPACITY)
+    cfg = h.hetm_config_default()
+    assert cfg.ws_chunk_bytes == 16384 and cfg.log_chunk_bytes == 49152
+    assert cfg.lock_log2 == 22 and cfg.max_batches == 4096
+
+
+def test_record_layouts_match_workloads():
+    import paper_1905_00661_b300 as h
+    import workloads as wl
+    assert h.LOG_DTYPE == wl.LOG_DTYPE
+    assert ctypes.sizeof(h.hetm_batch) == 48
+    assert ctypes.sizeof(h.hetm_config) == 112
+
+
+def test_init_rejects_bad_arguments_before_touching_the_device():
+    import paper_1905_00661_b300 as h
+    L = h.lib()
+    p = ctypes.c_void_p()
+    assert L.hetm_init(ctypes.byref(p), 0, 64, None, None) == h.HETM_EINVAL
+    assert L.hetm_init(ctypes.byref(p), 1024, 48, None, None) == h.HETM_EINVAL
+    assert L.hetm_init(ctypes.byref(p), 1 << 32, 64, None, None) == h.HETM_EINVAL
+    cfg = h.hetm_config_default()
+    cfg.ws_chunk_bytes = 100
+    assert L.hetm_init(ctypes.byref(p), 1024, 64, ctypes.byref(cfg), None) == h.HETM_EINVAL

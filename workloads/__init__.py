@@ -292,6 +292,14 @@ def init_words(seed: int, start: int, count: int) -> np.ndarray:
     return (draws_range(seed, S.INIT, count, start) >> np.uint64(32)).astype(np.uint32).view(np.int32)
 
 
+def init_stmr(seed: int, n: int, chunk: int = 1 << 24) -> np.ndarray:
+    """``init_words`` for the whole STMR, generated in bounded-memory chunks."""
+    out = np.empty(n, dtype=np.int32)
+    for s in range(0, n, chunk):
+        out[s:s + chunk] = init_words(seed, s, min(chunk, n - s))
+    return out
+
+
 def validation_round(seed: int = 1, log2_words: int = 28, granule_bytes: int = 64,
                      read_frac: float = 0.05, n_log: int = 1 << 24, hit_frac: float = 0.02,
                      zipf_q: float = 0.9, write_frac_of_read: float = 0.20,
@@ -354,7 +362,7 @@ def validation_round(seed: int = 1, log2_words: int = 28, granule_bytes: int = 6
                   + np.arange(wpg, dtype=np.uint64)[None, :]).reshape(-1).astype(np.uint32)
     plant_value = (draws_range(seed, S.PLANT_VAL, plant_addr.size) >> np.uint64(32)).astype(
         np.uint32).view(np.int32)
-    init = init_words(seed, 0, n_words) if with_init else None
+    init = init_stmr(seed, n_words) if with_init else None
     return ValidationRound(log2_words, granule_bytes, init, read_g, plant_addr, plant_value,
                            log, n_hit, meta={"n_read_granules": n_read,
                                              "n_plant_granules": n_plant_g})
