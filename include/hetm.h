@@ -233,6 +233,36 @@ HETM_API int hetm_validate(hetm_ctx *ctx, uint64_t *n_conflicts, uint32_t *dev_f
 HETM_API int hetm_validate_only(hetm_ctx *ctx, const hetm_log_entry *dev_log, uint64_t n,
                        uint32_t *dev_flag_bits, uint64_t *dev_count);
 
+/* Allocation-free validation (no counterpart in the paper: the paper's
+ * validation always runs inside its own runtime, which owns its memory).
+ * For callers that must not allocate device memory at the moment they
+ * validate: work recorded into a CUDA graph under capture, serving loops
+ * that cannot afford cudaMalloc's device-wide synchronization, and plug-ins
+ * whose host framework hands them only input and output buffers.  It needs
+ * no context: the same per-tuple test as hetm_validate_only is run against
+ * the caller's RS_bmp (dev_rs_bmp, bit g of word g/32, for a STMR of
+ * stmr_words words and conflict granule granule_bytes).
+ *   dev_log          device, 16-byte aligned, n tuples (n <= HETM_NOALLOC_MAX_TUPLES,
+ *                    else HETM_ECAPACITY)
+ *   dev_flag_bits    device, ceil(n/32) words, or NULL
+ *   dev_n_conflicts  device uint64: receives (not adds) the number of hits
+ *   dev_err          device int32 or NULL: HETM_OK, or HETM_EDEVICE when a
+ *                    tuple's address was >= stmr_words (that tuple is skipped)
+ *   stream           cudaStream_t (NULL = legacy default stream)
+ * Asynchronous; calls no cudaMalloc, cudaFree or allocating library routine.
+ * Its scratch is one static device array of about 48 KiB per GPU that loads
+ * the library, kept until the process exits and shared by every call on
+ * that GPU: calls that overlap on the GPU (different streams without
+ * ordering) race on it and give undefined results.  Each call rewrites every
+ * scratch slot it reads, so nothing needs clearing between calls.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture begins. */
+#define HETM_NOALLOC_MAX_TUPLES (1ull << 25)
+HETM_API int hetm_validate_noalloc(const hetm_log_entry *dev_log, uint64_t n,
+                                   const uint32_t *dev_rs_bmp, uint32_t granule_bytes,
+                                   uint64_t stmr_words, uint32_t *dev_flag_bits,
+                                   uint64_t *dev_n_conflicts, int32_t *dev_err, void *stream);
+
 /* -------------------------------------------------------- merge (A6) */
 /* Copy the WS_bmp chunks W -> S (conflict == 0) or S -> W (conflict == 1);
  * conflict == -1 takes the decision from the last hetm_validate on the

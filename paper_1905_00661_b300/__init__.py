@@ -64,7 +64,7 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_read_stmr", "hetm_device_ptr", "hetm_bitmap_words", "hetm_sync",
            "hetm_gpu_submit_batch", "hetm_gpu_exec", "hetm_exec_counters", "hetm_gpu_mark",
            "hetm_cpu_log_write", "hetm_log_attach", "hetm_validate", "hetm_validate_only",
-           "hetm_merge", "hetm_round")
+           "hetm_merge", "hetm_round", "hetm_validate_noalloc")
 
 
 class HetmError(RuntimeError):
@@ -95,6 +95,7 @@ def _declare(L):
         "hetm_validate_only": (_int, [_vp, _vp, _u64, _vp, _vp]),
         "hetm_merge": (_int, [_vp, _int]),
         "hetm_round": (_int, [_vp, P(hetm_round_stats)]),
+        "hetm_validate_noalloc": (_int, [_vp, _u64, _vp, _u32, _u64, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -159,6 +160,18 @@ class _CudaArray:
     def __init__(self, ptr, n, typestr):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
                                          "version": 3, "strides": None}
+
+
+HETM_NOALLOC_MAX_TUPLES = 1 << 25
+
+
+def hetm_validate_noalloc(dev_log, n, dev_rs_bmp, granule_bytes, stmr_words, dev_flag_bits,
+                          dev_n_conflicts, dev_err=None, stream=None):
+    """Allocation-free validation (see include/hetm.h): device pointers or tensors in,
+    hit count (and optional error code) written to device memory; returns the C status."""
+    return _lib.hetm_validate_noalloc(_ptr(dev_log), n, _ptr(dev_rs_bmp), granule_bytes,
+                                      stmr_words, _ptr(dev_flag_bits), _ptr(dev_n_conflicts),
+                                      _ptr(dev_err), stream)
 
 
 # ---------------------------------------------------------------------------

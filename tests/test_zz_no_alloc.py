@@ -1,0 +1,61 @@
+"""hetm_validate_noalloc against hetm_validate_only.
+
+The allocation-free entry point serves callers that cannot allocate device
+memory when they validate -- work being captured into a CUDA graph, serving
+loops that must not pay cudaMalloc's device-wide synchronization, plug-ins
+whose host framework owns all device memory.  It keeps its scratch in one
+static device array shared by every call, so the check runs two calls in a
+row (a large log, then a shorter one that must not see the first call's
+leftovers) and compares flags, hit count and status with the context-based
+entry point on the same inputs.  Integer results: they must match exactly.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from roundkit import flags_of, to_dev
+
+
+def test_noalloc_rejects_oversized_input_without_device_work():
+    import paper_1905_00661_b300 as h
+    rc = h.lib().hetm_validate_noalloc(None, h.HETM_NOALLOC_MAX_TUPLES + 1, None, 64, 1 << 20,
+                                       None, None, None, None)
+    assert rc == h.HETM_ECAPACITY
+    assert h.lib().hetm_validate_noalloc(None, 0, None, 48, 1 << 20, None, None, None,
+                                         None) == h.HETM_EINVAL
+
+
+@pytest.mark.gpu
+def test_noalloc_matches_validate_only_on_two_calls(hetm):
+    import torch
+    h = hetm
+    v = wl.validation_round(seed=12, log2_words=20, n_log=300001)  # 37 blocks, ragged end
+    n_words = 1 << 20
+    with h.Context(n_words, v.granule_bytes) as ctx:
+        first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
+        ctx.gpu_mark(torch.from_numpy(first).cuda())
+        rs = ctx.device_tensor(h.RS_BMP)
+        dlog = to_dev(torch, v.log)
+        stream = ctx.stream
+        for n in (len(v.log), 20011):  # second call: shorter log, scratch reused
+            words = (n + 31) // 32
+            ref_flags = torch.zeros(words, dtype=torch.int32, device="cuda")
+            ref_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            ctx.validate_only(dlog, n, ref_flags, ref_cnt)
+            flags = torch.full((words,), -1, dtype=torch.int32, device="cuda")
+            cnt = torch.full((1,), 12345, dtype=torch.int64, device="cuda")
+            err = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            rc = h.hetm_validate_noalloc(dlog, n, rs, v.granule_bytes, n_words, flags, cnt, err,
+                                         stream.cuda_stream)
+            assert rc == h.HETM_OK
+            stream.synchronize()
+            assert int(err.item()) == h.HETM_OK
+            assert int(cnt.item()) == int(ref_cnt.item())
+            got = flags_of(flags.cpu().numpy().view(np.uint32), n)
+            exp = flags_of(ref_flags.cpu().numpy().view(np.uint32), n)
+            np.testing.assert_array_equal(got, exp)
+        # the planted recipe fixes the hit count of the full log
+        assert int(ref_cnt.item()) > 0
