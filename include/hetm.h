@@ -104,6 +104,18 @@ typedef struct hetm_cache_req {
 } hetm_cache_req;
 
 /* ---------------------------------------------------------- configuration */
+/* GPU guest TM of the execution phase (any TM that keeps committed
+ * transactions serializable may serve, Sec. IV-B):
+ *   ORDERED    -- the serial order is fixed before execution: W1 read-only
+ *                 transactions first (lock-free, on the phase-start state),
+ *                 then every other transaction in index order, each running
+ *                 when its declared words / cache set reach its turn.  No
+ *                 aborts.  Needs max_round_tx capacity (~200 B per tx).
+ *   OPTIMISTIC -- word-based STM with striped version locks (try-lock for
+ *                 known write sets, validated reads, bounded retries). */
+#define HETM_EXEC_ORDERED 0
+#define HETM_EXEC_OPTIMISTIC 1
+
 typedef struct hetm_config {
     uint32_t ws_chunk_bytes;   /* WS_bmp / merge chunk, power of two >= 16
                                   (Sec. IV-D uses 16 KB); default 16384    */
@@ -119,6 +131,9 @@ typedef struct hetm_config {
     uint32_t max_batches;      /* pending batches per round; 4096          */
     uint32_t cache_log2_sets;  /* object-cache layout (HETM_WL_CACHE)      */
     uint64_t cache_key_base, cache_val_base, cache_lru_base, cache_ver_base;
+    uint32_t exec_mode;        /* HETM_EXEC_ORDERED (default) or HETM_EXEC_OPTIMISTIC */
+    uint32_t reserved0;
+    uint64_t max_round_tx;     /* ordered mode: transactions per execution phase; 1<<22 */
     /* Optional device allocator (e.g. a framework's caching allocator);
      * NULL = cudaMalloc/cudaFree.  Called only from hetm_init/hetm_destroy. */
     void *(*dev_alloc)(size_t bytes, void *user);

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libhetm.so")
 HETM_OK, HETM_EINVAL, HETM_ENOMEM, HETM_ECAPACITY = 0, -1, -2, -3
 HETM_ETIMEOUT, HETM_ECUDA, HETM_EBUSY, HETM_EDEVICE = -4, -5, -6, -7
 HETM_WL_BANK, HETM_WL_RMW, HETM_WL_CACHE = 1, 2, 3
+HETM_EXEC_ORDERED, HETM_EXEC_OPTIMISTIC = 0, 1
 STMR_W, STMR_S, TS, RS_BMP, WS_BMP = 0, 1, 2, 3, 4
 
 LOG_DTYPE = np.dtype([("addr", "<u4"), ("value", "<i4"), ("ts", "<u4")])
@@ -39,7 +40,8 @@ class hetm_config(ctypes.Structure):
                 ("cpu_threads", _u32), ("log_chunk_bytes", _u32), ("log_capacity", _u64),
                 ("cpu_log_capacity", _u64), ("max_batches", _u32), ("cache_log2_sets", _u32),
                 ("cache_key_base", _u64), ("cache_val_base", _u64), ("cache_lru_base", _u64),
-                ("cache_ver_base", _u64), ("dev_alloc", _ALLOC), ("dev_free", _FREE),
+                ("cache_ver_base", _u64), ("exec_mode", _u32), ("reserved0", _u32),
+                ("max_round_tx", _u64), ("dev_alloc", _ALLOC), ("dev_free", _FREE),
                 ("alloc_user", _vp)]
 
 

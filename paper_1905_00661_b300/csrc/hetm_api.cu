@@ -109,6 +109,8 @@ struct hetm_ctx {
     cudaGraphExec_t g_exec = nullptr, g_sync = nullptr;
     cudaEvent_t ev[7] = {};  // round timing: 0/6 around the executor, 1..4 in the sync graph, 5 end
 
+    OrderArgs ord{};               // ordered-executor scratch (exec_mode ORDERED)
+    int ord_blocks = 0;
     int exec_blocks = 0, exec_threads = 256, stream_blocks = 0;
     unsigned long long prev_counters[3] = {0, 0, 0};
 
@@ -279,6 +281,19 @@ ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
 // Executor launch(es) for the staged table: one persistent launch over all
 // batches, or one launch per batch.
 int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb) {
+    if (c->cfg.exec_mode == HETM_EXEC_ORDERED) {
+        OrderArgs o = c->ord;
+        if (!per_batch) {
+            o.e = exec_args(c, c->d_round, c->d_batches, c->d_prefix);
+            CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream));
+            return HETM_OK;
+        }
+        for (uint32_t b = 0; b < nb; ++b) {
+            o.e = exec_args(c, c->d_round + 1 + b, c->d_batches + b, c->d_prefix0);
+            CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream));
+        }
+        return HETM_OK;
+    }
     if (!per_batch) {
         CK(cudaMemsetAsync(&c->scr->next, 0, sizeof(unsigned long long), c->stream));
         CK(launch_exec(exec_args(c, c->d_round, c->d_batches, c->d_prefix), c->exec_blocks,
@@ -362,6 +377,8 @@ int hetm_config_default(hetm_config *cfg) {
     cfg->log_capacity = 1ull << 24;
     cfg->cpu_log_capacity = 1ull << 21;
     cfg->max_batches = 4096;
+    cfg->exec_mode = HETM_EXEC_ORDERED;
+    cfg->max_round_tx = 1ull << 22;
     return HETM_OK;
 }
 
@@ -409,8 +426,12 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
     if (d.lock_log2 < 1 || d.lock_log2 > 30 || d.lock_shift > 31) return HETM_EINVAL;
     if (d.exec_threads == 0 || d.exec_threads % 32 || d.exec_threads > 256) return HETM_EINVAL;
     if (d.log_chunk_bytes < 12 || d.log_chunk_bytes % 12 || d.max_attempts == 0) return HETM_EINVAL;
-    if (d.max_batches == 0 || d.cpu_threads == 0 || d.log_capacity == 0) return HETM_EINVAL;
+    if (d.max_batches == 0 || d.max_batches > 65535 || d.cpu_threads == 0 || d.log_capacity == 0)
+        return HETM_EINVAL;
     if (d.cache_log2_sets > 28) return HETM_EINVAL;
+    if (d.exec_mode > HETM_EXEC_OPTIMISTIC) return HETM_EINVAL;
+    if (d.exec_mode == HETM_EXEC_ORDERED && (d.max_round_tx == 0 || d.max_round_tx > (1ull << 28)))
+        return HETM_EINVAL;
 
     hetm_ctx *c = new (std::nothrow) hetm_ctx();
     if (!c) return HETM_ENOMEM;
@@ -450,6 +471,25 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         !dev_alloc_t(c, &c->d_prefix0, 2) || !dev_alloc_t(c, &c->dlog[0], d.log_capacity) ||
         !dev_alloc_t(c, &c->dlog[1], d.log_capacity))
         return fail(HETM_ENOMEM);
+    if (d.exec_mode == HETM_EXEC_ORDERED) {
+        OrderArgs &o = c->ord;
+        o.cap_tx = (uint32_t)d.max_round_tx;
+        o.cap_acc = 4 * o.cap_tx;
+        o.key_bits = (uint32_t)ilog2(stmr_words);
+        if (o.key_bits == 0) o.key_bits = 1;
+        const uint64_t hist_n = 256ull * ((o.cap_acc + 2047) / 2048);
+        const uint64_t tot_n = std::max<uint64_t>(hist_n, o.cap_acc) / 1024 + 2;
+        if (!dev_alloc_t(c, &o.cnt, o.cap_tx) || !dev_alloc_t(c, &o.scan_tot, tot_n) ||
+            !dev_alloc_t(c, &o.keys0, o.cap_acc) || !dev_alloc_t(c, &o.vals0, o.cap_acc) ||
+            !dev_alloc_t(c, &o.keys1, o.cap_acc) || !dev_alloc_t(c, &o.vals1, o.cap_acc) ||
+            !dev_alloc_t(c, &o.hist, hist_n) || !dev_alloc_t(c, &o.runs, o.cap_acc) ||
+            !dev_alloc_t(c, &o.rec, o.cap_tx) || !dev_alloc_t(c, &o.packed, o.cap_acc) ||
+            !dev_alloc_t(c, &o.n_acc, 4) ||
+            !dev_alloc_t(c, &o.v0, 1))
+            return fail(HETM_ENOMEM);
+        o.n_ord = o.n_acc + 1;
+        o.n_tx32 = o.n_acc + 2;
+    }
     for (auto &s : c->stage) {
         if (!host_alloc_t(&s.rounds, nb + 1) || !host_alloc_t(&s.batches, nb) ||
             !host_alloc_t(&s.prefix, nb + 1))
@@ -474,6 +514,9 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
     c->exec_threads = (int)d.exec_threads;
     if (exec_occupancy(c->exec_threads, &occ) != 0 || occ < 1) occ = 1;
     c->exec_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ;
+    int occ_o = 0;
+    if (ordered_exec_occupancy(&occ_o) != 0 || occ_o < 1) occ_o = 1;
+    c->ord_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ_o;
     c->stream_blocks = c->n_sm * 8;
 
     if (cudaMemsetAsync(c->locks, 0, (1ull << d.lock_log2) * 8, c->stream) != cudaSuccess ||
@@ -570,6 +613,11 @@ int hetm_gpu_submit_batch(hetm_ctx *c, const hetm_batch *b, uint64_t *batch_id) 
             return HETM_EINVAL;
     }
     if (c->pending.size() >= c->cfg.max_batches) return HETM_EBUSY;
+    if (c->cfg.exec_mode == HETM_EXEC_ORDERED) {
+        uint64_t queued = b->n_tx;
+        for (const auto &p : c->pending) queued += p.n_tx;
+        if (queued > c->cfg.max_round_tx) return HETM_EBUSY;
+    }
     DevBatch d{b->workload, b->n_tx, b->tx, b->order, b->status, b->out, b->txid_base, b->word_base};
     c->pending.push_back(d);
     if (batch_id) *batch_id = c->next_batch_id++;

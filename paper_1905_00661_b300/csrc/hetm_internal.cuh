@@ -62,6 +62,43 @@ struct ExecArgs {
     uint64_t key_base, val_base, lru_base, ver_base;
 };
 
+// One transaction of the ordered phase (indexed by its rank in that phase).
+// Slot k of a word transaction is one distinct word; turn[k] carries the
+// access's position among the accesses to its resource plus flags.
+constexpr uint32_t kSeg = 256;              // transactions per CTA segment
+constexpr uint32_t kTurnMask = 0x0FFFFFFFu;
+constexpr uint32_t kFWriter = 1u << 31;     // the access writes the resource
+constexpr uint32_t kFLast = 1u << 30;       // last access of the word in the launch
+constexpr uint32_t kFLocal = 1u << 29;      // predecessor is in the same segment
+constexpr uint32_t kFPublish = 1u << 28;    // successor is in a later segment
+struct __align__(16) OrdRec {
+    uint32_t u;        // launch index
+    uint32_t meta;     // n (bits 0-2) | workload (3-4) | map (8-15) | batch (16-31)
+    uint32_t aux;      // W1: txid; bank: amount
+    uint32_t li;       // index inside its batch
+    uint32_t addr[4];  // distinct words (bank: src, dst); cache: set version word
+    uint32_t res[4];   // resource id (index of its run in the sorted access list)
+    uint32_t turn[4];  // position | flags
+    uint32_t src[4];   // local predecessor: (thread << 2) | slot
+};
+static_assert(sizeof(OrdRec) == 80, "80-byte record");
+
+// Scratch of the ordered executor (capacities fixed at context creation).
+struct OrderArgs {
+    ExecArgs e;
+    uint64_t *cnt;              // [cap_tx] per-tx (1 << 32 | #resources) -> exclusive prefix
+    uint64_t *scan_tot;         // per-tile totals of the scans
+    uint32_t *keys0, *vals0;    // [cap_acc] access list, sorted in place
+    uint32_t *keys1, *vals1;    // [cap_acc] radix-sort ping-pong buffers
+    uint64_t *hist;             // [256 * ceil(cap_acc / 2048)] digit counts
+    uint64_t *runs;             // [cap_acc] (run head << 32 | last writer + 1), max-scanned
+    OrdRec *rec;                // [cap_tx] ordered-phase transactions by rank
+    unsigned long long *packed; // [cap_acc] per resource: (turns done << 32) | value
+    uint32_t *n_acc, *n_ord, *n_tx32;
+    unsigned long long *v0;     // commit clock before the launch
+    uint32_t cap_tx, cap_acc, key_bits;
+};
+
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ unsigned long long ld_rlx64(const unsigned long long *p) {
     unsigned long long v;
@@ -123,6 +160,8 @@ __device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
 // ----------------------------------------------------------- host launchers
 cudaError_t launch_exec(const ExecArgs &a, int blocks, int threads, cudaStream_t s);
 int exec_occupancy(int threads, int *blocks_per_sm);
+cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks, cudaStream_t s);
+int ordered_exec_occupancy(int *blocks_per_sm);
 
 cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
                             uint64_t n_words, uint32_t *flags, unsigned long long *count,

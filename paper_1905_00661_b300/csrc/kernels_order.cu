@@ -1,0 +1,866 @@
+// Ordered execution of a batch (execution phase, Sec. IV-C), the default
+// GPU guest TM of this library.
+//
+// The paper lets any TM that keeps committed transactions serializable and
+// every running transaction consistent drive the GPU side (Sec. IV-B); here
+// the serial order is fixed up front instead of discovered by aborts:
+//
+//   1. read-only W1 transactions of the launch come first in the order: they
+//      all observe the launch-start state, take no locks and never wait;
+//   2. every other transaction (W1 updates, bank transfers, cache requests)
+//      follows in launch index order.  Each names its resources up front
+//      (its words; a cache request its set).  A stable radix sort of the
+//      (resource, index) pairs gives, for every access, its position among
+//      the accesses to that resource; a transaction runs when every resource
+//      has reached its position, so each one executes atomically at its
+//      place in the order and nothing ever aborts or rolls back.
+//   3. for word resources the last writer hands the next one the word's
+//      value inside a packed (count, value) word, so one 8-byte store
+//      publishes both the turn and the data; cache sets use reader/writer
+//      turns (GETs of one set run concurrently, PUTs alone).
+//
+// Commit keys: 2*V0 + 1 for the read-only phase (V0 = commit clock before the
+// launch), 2*(V0 + 1 + u) for transaction u of the ordered phase; the clock
+// then advances by the launch size.  RS_bmp / WS_bmp are recorded at commit
+// exactly as in the optimistic executor.
+//
+// Every wait is a poll inside the warp's iteration, bounded by a wall-clock
+// budget; transactions are handed out in index order to resident warps, so
+// the lowest unfinished transaction can always run.
+
+#include "hetm_internal.cuh"
+
+namespace hetm {
+namespace {
+
+// ----------------------------------------------------------------------------
+// block-wide inclusive scan of one 64-bit value per thread (256 threads)
+// ----------------------------------------------------------------------------
+struct SumOp {
+    __device__ __forceinline__ uint64_t operator()(uint64_t a, uint64_t b) const { return a + b; }
+};
+struct PairMaxOp {  // independent max of the high and low 32-bit halves
+    __device__ __forceinline__ uint64_t operator()(uint64_t a, uint64_t b) const {
+        const uint32_t hi = max((uint32_t)(a >> 32), (uint32_t)(b >> 32));
+        const uint32_t lo = max((uint32_t)a, (uint32_t)b);
+        return ((uint64_t)hi << 32) | lo;
+    }
+};
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;                        // per thread
+constexpr int kScanTile = kScanThreads * kScanItems; // 1024 items per block
+
+template <class Op>
+__device__ __forceinline__ uint64_t block_scan_incl(uint64_t v, Op op, uint64_t *s_warp) {
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(kFull, v, o);
+        if ((int)lane >= o) v = op(t, v);
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < kScanThreads / 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(kFull, w, o);
+            if ((int)lane >= o) w = op(t, w);
+        }
+        if (lane < kScanThreads / 32) s_warp[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) v = op(s_warp[warp - 1], v);
+    __syncthreads();
+    return v;
+}
+
+// Tile-local inclusive scan of in[0..n) (n read from *n_dev); tile totals
+// to tot[block].  For kExclusive the written value is the exclusive prefix.
+template <class Op, bool kExclusive>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint64_t *in, uint64_t *out,
+                                                             const uint32_t *n_dev, uint32_t n_fix,
+                                                             uint64_t *tot, uint64_t identity) {
+    __shared__ uint64_t s_warp[kScanThreads / 32];
+    const uint32_t n = n_dev ? *n_dev : n_fix;
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    if (base >= n) return;
+    Op op;
+    uint64_t x[kScanItems];
+    uint64_t run = identity;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint64_t i = base + threadIdx.x * kScanItems + k;
+        x[k] = i < n ? in[i] : identity;
+        run = op(run, x[k]);
+    }
+    const uint64_t incl = block_scan_incl(run, op, s_warp);
+    uint64_t pre = __shfl_up_sync(kFull, incl, 1);
+    // exclusive prefix of this thread's items inside the tile
+    {
+        const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+        if (lane == 0) pre = warp == 0 ? identity : s_warp[warp - 1];
+        // s_warp was overwritten by the scan with inclusive warp totals
+    }
+    uint64_t acc = pre;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint64_t i = base + threadIdx.x * kScanItems + k;
+        const uint64_t nxt = op(acc, x[k]);
+        if (i < n) out[i] = kExclusive ? acc : nxt;
+        acc = nxt;
+    }
+    if (threadIdx.x == kScanThreads - 1) tot[blockIdx.x] = incl;
+}
+
+// Exclusive scan of the tile totals in place (one block, any count).
+template <class Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_totals(uint64_t *tot, const uint32_t *n_dev,
+                                                              uint32_t n_fix, uint64_t identity) {
+    __shared__ uint64_t s_warp[kScanThreads / 32];
+    __shared__ uint64_t s_carry;
+    const uint32_t n = n_dev ? *n_dev : n_fix;
+    const uint32_t nt = (n + kScanTile - 1) / kScanTile;
+    Op op;
+    if (threadIdx.x == 0) s_carry = identity;
+    __syncthreads();
+    for (uint32_t b0 = 0; b0 < nt; b0 += kScanThreads) {
+        const uint32_t b = b0 + threadIdx.x;
+        const uint64_t v = b < nt ? tot[b] : identity;
+        const uint64_t incl = block_scan_incl(v, op, s_warp);
+        const uint64_t carry = s_carry;
+        uint64_t ex = __shfl_up_sync(kFull, incl, 1);
+        const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+        if (lane == 0) ex = warp == 0 ? identity : s_warp[warp - 1];
+        __syncthreads();
+        if (b < nt) tot[b] = op(carry, ex);
+        if (threadIdx.x == kScanThreads - 1) s_carry = op(carry, incl);
+        __syncthreads();
+    }
+}
+
+// out[i] = op(tot[tile], out[i]) for every item.
+template <class Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_fix(uint64_t *out, const uint32_t *n_dev,
+                                                           uint32_t n_fix, const uint64_t *tot) {
+    const uint32_t n = n_dev ? *n_dev : n_fix;
+    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+    if (base >= n) return;
+    Op op;
+    const uint64_t c = tot[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint64_t i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = op(c, out[i]);
+    }
+}
+
+}  // namespace
+
+// Device-wide scan of n (device or fixed) 64-bit values; `grid` covers the
+// capacity in tiles of kScanTile; tot holds one value per tile.
+template <class Op, bool kExclusive>
+static cudaError_t device_scan(const uint64_t *in, uint64_t *out, const uint32_t *n_dev,
+                               uint32_t n_fix, uint32_t grid, uint64_t *tot, uint64_t identity,
+                               cudaStream_t s) {
+    k_scan_tiles<Op, kExclusive><<<grid, kScanThreads, 0, s>>>(in, out, n_dev, n_fix, tot, identity);
+    k_scan_totals<Op><<<1, kScanThreads, 0, s>>>(tot, n_dev, n_fix, identity);
+    k_scan_fix<Op><<<grid, kScanThreads, 0, s>>>(out, n_dev, n_fix, tot);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// ----------------------------------------------------------------------------
+// stable LSD radix sort of (key, value) u32 pairs, 8-bit digits
+// ----------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
+
+// hist[d * n_tiles_cap + tile] = count of digit d in the tile
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *keys, const uint32_t *n_dev,
+                                                             uint32_t shift, uint64_t *hist,
+                                                             uint32_t n_tiles_cap) {
+    __shared__ uint32_t s_cnt[256];
+    const uint32_t n = *n_dev;
+    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    if (base < n) {
+#pragma unroll
+        for (int k = 0; k < kSortItems; ++k) {
+            const uint64_t i = base + k * kSortThreads + threadIdx.x;
+            if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 255u], 1u);
+        }
+    }
+    __syncthreads();
+    hist[(uint64_t)threadIdx.x * n_tiles_cap + blockIdx.x] = s_cnt[threadIdx.x];
+}
+
+// Stable scatter: items keep their input order within a digit.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
+                                                                uint32_t *kout, uint32_t *vout,
+                                                                const uint32_t *n_dev, uint32_t shift,
+                                                                const uint64_t *hist_ex,
+                                                                uint32_t n_tiles_cap) {
+    __shared__ uint32_t s_base[256];                      // running output position per digit
+    __shared__ uint32_t s_wcnt[kSortThreads / 32][256];   // per-warp digit counts of a round
+    const uint32_t n = *n_dev;
+    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+    if (base >= n) return;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    s_base[threadIdx.x] = (uint32_t)hist_ex[(uint64_t)threadIdx.x * n_tiles_cap + blockIdx.x];
+    for (int r = 0; r < kSortItems; ++r) {
+        for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
+        const bool ok = i < n;
+        const uint32_t key = ok ? kin[i] : 0u;
+        const uint32_t val = ok ? vin[i] : 0u;
+        const uint32_t d = ok ? (key >> shift) & 255u : 256u + lane;  // padding: unique
+        const unsigned peers = __match_any_sync(kFull, d);
+        const uint32_t rank = __popc(peers & lanemask_lt());
+        if (ok && rank == 0) s_wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        // digit-wise exclusive prefix over the warps of this round
+        uint32_t run = 0;
+        {
+            const uint32_t dd = threadIdx.x;
+            for (int w = 0; w < kSortThreads / 32; ++w) {
+                const uint32_t c = s_wcnt[w][dd];
+                s_wcnt[w][dd] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        if (ok) {
+            const uint32_t pos = s_base[d] + s_wcnt[warp][d] + rank;
+            if (pos < n) {  // always true for a consistent histogram
+                kout[pos] = key;
+                vout[pos] = val;
+            }
+        }
+        __syncthreads();
+        s_base[threadIdx.x] += run;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// Sort n (device) pairs by key, `bits` significant key bits, in place in
+// (k0, v0) using (k1, v1) as the other buffer.  hist holds 256 *
+// n_tiles_cap values; tot one value per scan tile of it.
+static cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
+                              const uint32_t *n_dev, uint32_t cap, uint32_t bits, uint64_t *hist,
+                              uint64_t *tot, cudaStream_t s) {
+    const uint32_t n_tiles_cap = (cap + kSortTile - 1) / kSortTile;
+    const uint32_t hist_n = 256u * n_tiles_cap;
+    const uint32_t scan_grid = (hist_n + kScanTile - 1) / kScanTile;
+    uint32_t passes = (bits + 7) / 8;
+    if (passes & 1u) ++passes;  // even pass count: the result lands back in (k0, v0)
+    for (uint32_t p = 0; p < passes; ++p) {
+        const uint32_t shift = 8 * p;
+        uint32_t *ki = (p & 1) ? k1 : k0, *vi = (p & 1) ? v1 : v0;
+        uint32_t *ko = (p & 1) ? k0 : k1, *vo = (p & 1) ? v0 : v1;
+        if (shift >= 32) {  // padding pass: plain copy keeps the order
+            cudaError_t e = cudaMemcpyAsync(ko, ki, (size_t)cap * 4, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            e = cudaMemcpyAsync(vo, vi, (size_t)cap * 4, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        k_radix_hist<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, n_dev, shift, hist, n_tiles_cap);
+        cudaError_t e = device_scan<SumOp, true>(hist, hist, nullptr, hist_n, scan_grid, tot, 0, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, hist,
+                                                             n_tiles_cap);
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Resources (conflict units) of transaction u for the ordered phase: its
+// distinct words for bank / W1 updates (all written), its set's version word
+// for a cache request (PUT writes, GET reads).  W1 read-only transactions
+// have none: they run in the read-only phase.
+struct TxView {
+    uint32_t wl, li, b, n;
+    uint32_t addr[4];
+    uint32_t wmask;    // bit k: resource k is written
+    uint32_t map;      // W1: 2-bit slot of the j-th declared word
+    uint32_t aux;      // W1: txid; bank: amount
+    const DevBatch *d;
+};
+
+__device__ __forceinline__ int find_batch(const uint64_t *prefix, uint32_t nb, uint64_t gi) {
+    uint32_t lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= gi) lo = mid; else hi = mid;
+    }
+    return (int)lo;
+}
+
+__device__ __forceinline__ bool view_tx(const ExecArgs &a, uint64_t u, TxView &t) {
+    t.b = (uint32_t)find_batch(a.prefix, a.rp->n_batches, u);
+    t.d = a.batches + t.b;
+    t.wl = t.d->workload;
+    t.li = (uint32_t)(u - a.prefix[t.b]);
+    t.n = 0;
+    t.wmask = 0;
+    t.map = 0;
+    t.aux = 0;
+    if (t.wl == HETM_WL_BANK) {
+        const hetm_bank_tx x = static_cast<const hetm_bank_tx *>(t.d->tx)[t.li];
+        t.addr[0] = t.d->word_base + x.src;
+        t.addr[1] = t.d->word_base + x.dst;
+        t.n = t.addr[1] == t.addr[0] ? 1 : 2;
+        t.wmask = 3;
+        t.aux = (uint32_t)x.amount;
+        return t.addr[0] < a.n_words && t.addr[1] < a.n_words;
+    }
+    if (t.wl == HETM_WL_RMW) {
+        const hetm_rmw_tx *x = static_cast<const hetm_rmw_tx *>(t.d->tx) + t.li;
+        uint32_t orig[4];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            orig[j] = x->addr[j];
+            ok &= orig[j] < a.n_words;
+        }
+        if (x->flags & 1u) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t slot = m;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < (int)m && t.addr[k] == orig[j]) slot = k;
+                if (slot == m) t.addr[m++] = orig[j];
+                t.map |= slot << (2 * j);
+            }
+            t.n = m;
+            t.wmask = (1u << m) - 1;
+            t.aux = t.d->txid_base + t.li;
+        }
+        return ok;
+    }
+    if (t.wl == HETM_WL_CACHE) {
+        const hetm_cache_req *r = static_cast<const hetm_cache_req *>(t.d->tx) + t.li;
+        const uint32_t set = (uint32_t)(splitmix_fin(r->key) & ((1ull << a.cache_log2_sets) - 1));
+        t.addr[0] = (uint32_t)(a.ver_base + set);
+        t.n = 1;
+        t.wmask = r->op == 1 ? 1u : 0u;
+        return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(256) k_ord_count(OrderArgs o) {
+    const ExecArgs &a = o.e;
+    const uint64_t total = a.rp->total_tx;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        *o.n_tx32 = (uint32_t)total;
+        const unsigned long long v0 = *a.gv;
+        *o.v0 = v0;
+        *a.gv = v0 + total + 1;  // this launch owns versions v0+1 .. v0+total+1
+    }
+    unsigned long long bad = 0;
+    for (uint64_t u = tid; u < total; u += stride) {
+        TxView t;
+        const bool ok = view_tx(a, u, t);
+        o.cnt[u] = ok && t.n ? (1ull << 32) | t.n : 0ull;
+        if (!ok) {  // out-of-range words or unknown workload: not executed
+            if (t.d->status) t.d->status[t.li] = kGaveUp;
+            ++bad;
+        }
+    }
+    if (bad) {
+        set_err(a.err, kErrAddr);
+        atomicAdd(a.counters + 1, bad);
+    }
+}
+
+// access list entry: key = resource word, value = rank << 4 | slot << 2 | cache << 1 | writer
+__global__ void __launch_bounds__(256) k_ord_emit(OrderArgs o) {
+    const ExecArgs &a = o.e;
+    const uint64_t total = a.rp->total_tx;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < total; u += stride) {
+        TxView t;
+        const bool ok = view_tx(a, u, t);
+        const uint64_t c = o.cnt[u];  // exclusive prefix: (rank << 32) | offset
+        const uint32_t n = ok ? t.n : 0;
+        if (n) {
+            const uint32_t rank = (uint32_t)(c >> 32);
+            OrdRec &r = o.rec[rank];
+            r.u = (uint32_t)u;
+            r.meta = n | (t.wl << 3) | (t.map << 8) | (t.b << 16);
+            r.aux = t.aux;
+            r.li = t.li;
+            const uint32_t cache = t.wl == HETM_WL_CACHE ? 2u : 0u;
+            for (uint32_t k = 0; k < n; ++k) {
+                r.addr[k] = t.addr[k];
+                o.keys0[(uint32_t)c + k] = t.addr[k];
+                o.vals0[(uint32_t)c + k] = (rank << 4) | (k << 2) | cache | ((t.wmask >> k) & 1u);
+            }
+        }
+        if (u == total - 1) {
+            *o.n_acc = (uint32_t)c + n;
+            *o.n_ord = (uint32_t)(c >> 32) + (n ? 1u : 0u);
+        }
+    }
+    if (total == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        *o.n_acc = 0;
+        *o.n_ord = 0;
+    }
+}
+
+// per sorted access: (run head index << 32) | (index + 1 if a writer)
+__global__ void __launch_bounds__(256) k_ord_runs(OrderArgs o) {
+    const uint32_t n = *o.n_acc;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const bool head = i == 0 || o.keys0[i] != o.keys0[i - 1];
+        const bool writer = o.vals0[i] & 1u;
+        o.runs[i] = ((head ? i : 0ull) << 32) | (writer ? i + 1 : 0ull);
+        o.packed[i] = 0ull;
+    }
+}
+
+// Per access: resource id (its run head), its turn, and whether it takes its
+// input from a transaction of the same segment (then it does not wait on
+// the global turn) and must publish to a later segment.
+__global__ void __launch_bounds__(256) k_ord_acc(OrderArgs o) {
+    const uint32_t n = *o.n_acc;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t start = (uint32_t)(o.runs[i] >> 32);
+        const uint32_t v = o.vals0[i];
+        const uint32_t rank = v >> 4, k = (v >> 2) & 3u;
+        const bool cache = v & 2u, writer = v & 1u;
+        uint32_t turn, src = 0;
+        if (cache) {  // reader/writer turns on the set's counter
+            uint32_t need;
+            if (writer) {
+                need = (uint32_t)i - start;
+            } else {
+                const uint32_t lw = i ? (uint32_t)o.runs[i - 1] : 0u;  // last writer before i, + 1
+                need = lw > start ? lw - start : 0u;
+            }
+            turn = need | (writer ? kFWriter : 0u);
+        } else {
+            turn = ((uint32_t)i - start) | kFWriter;
+            if (i > start) {
+                const uint32_t pv = o.vals0[i - 1];
+                if ((pv >> 4) / kSeg == rank / kSeg) {
+                    turn |= kFLocal;
+                    src = (((pv >> 4) % kSeg) << 2) | ((pv >> 2) & 3u);
+                }
+            }
+            const bool last = i + 1 == n || o.keys0[i + 1] != o.keys0[i];
+            if (last) turn |= kFLast;
+            else if ((o.vals0[i + 1] >> 4) / kSeg != rank / kSeg) turn |= kFPublish;
+        }
+        OrdRec &r = o.rec[rank];
+        r.res[k] = start;
+        r.turn[k] = turn;
+        r.src[k] = src;
+    }
+}
+
+// Read-only phase: W1 read-only transactions on the launch-start state.
+__global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
+    const ExecArgs &a = o.e;
+    const uint64_t total = a.rp->total_tx;
+    const unsigned long long key = 2ull * (*o.v0) + 1;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    unsigned long long n_commit = 0;
+    // loop bound rounded up to whole warps so that the warp reduction below is convergent
+    const uint64_t span = (total + 31) & ~31ull;
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < span; u += stride) {
+        if (u >= total) continue;
+        const int b = find_batch(a.prefix, a.rp->n_batches, u);
+        const DevBatch &d = a.batches[b];
+        if (d.workload != HETM_WL_RMW) continue;
+        const uint32_t li = (uint32_t)(u - a.prefix[b]);
+        const hetm_rmw_tx *x = static_cast<const hetm_rmw_tx *>(d.tx) + li;
+        if (x->flags & 1u) continue;
+        uint32_t ad[4];
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ad[k] = x->addr[k];
+            ok &= ad[k] < a.n_words;
+        }
+        if (!ok) continue;  // reported by k_ord_count
+        int32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s += a.W[ad[k]];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            // hot words are read by many transactions: skip bits already set
+            const uint32_t g = ad[k] >> a.gshift, m = 1u << (g & 31);
+            if (!(a.rs[g >> 5] & m)) atomicOr(a.rs + (g >> 5), m);
+        }
+        if (d.order) d.order[li] = key;
+        if (d.out) static_cast<int32_t *>(d.out)[li] = s;
+        if (d.status) d.status[li] = kCommitted;
+        ++n_commit;
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) n_commit += __shfl_xor_sync(kFull, n_commit, w);
+    if ((threadIdx.x & 31u) == 0 && n_commit) atomicAdd(a.counters + 0, n_commit);
+}
+
+__device__ __forceinline__ void mark_range(const ExecArgs &a, uint64_t w0, uint32_t len, bool write) {
+    for (uint64_t g = w0 >> a.gshift; g <= (w0 + len - 1) >> a.gshift; ++g)
+        atomicOr(a.rs + (g >> 5), 1u << (g & 31));
+    if (write)
+        for (uint64_t c = w0 >> a.cshift; c <= (w0 + len - 1) >> a.cshift; ++c)
+            atomicOr(a.ws + (c >> 5), 1u << (c & 31));
+}
+
+__device__ __forceinline__ uint4 ld_volatile16(const int32_t *p) {
+    uint4 v;
+    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+
+// One cache request on its set, which this thread holds (PUT) or shares (GET).
+__device__ void cache_request(const ExecArgs &a, const hetm_cache_req &r, uint32_t stamp,
+                              uint64_t &out) {
+    const uint32_t set = (uint32_t)(splitmix_fin(r.key) & ((1ull << a.cache_log2_sets) - 1));
+    const uint64_t kw = a.key_base + 16ull * set;
+    uint64_t keys[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 v = ld_volatile16(a.W + kw + 4 * q);
+        keys[2 * q] = ((uint64_t)v.y << 32) | v.x;
+        keys[2 * q + 1] = ((uint64_t)v.w << 32) | v.z;
+    }
+    int hit = -1, empty = -1;
+#pragma unroll
+    for (int w = 7; w >= 0; --w) {
+        if (keys[w] == r.key) hit = w;
+        if (keys[w] == 0) empty = w;
+    }
+    mark_range(a, kw, 16, false);
+    if (r.op == 0) {
+        if (hit < 0) {
+            out = ~0ull;
+            return;
+        }
+        const uint64_t vw = a.val_base + 2ull * (8ull * set + hit);
+        const uint64_t lw = a.lru_base + 8ull * set + hit;
+        out = ld_rlx_u64(a.W + vw);
+        // GETs of a set run concurrently: their stamps grow with the serial
+        // order, so the max is the stamp of the last one
+        atomicMax(reinterpret_cast<unsigned int *>(a.W + lw), stamp);
+        mark_range(a, vw, 2, false);
+        mark_range(a, lw, 1, true);
+        return;
+    }
+    const uint64_t verw = a.ver_base + set;
+    uint32_t way;
+    if (hit >= 0) {
+        way = (uint32_t)hit;
+    } else if (empty >= 0) {
+        way = (uint32_t)empty;
+    } else {
+        const uint4 l0 = ld_volatile16(a.W + a.lru_base + 8ull * set);
+        const uint4 l1 = ld_volatile16(a.W + a.lru_base + 8ull * set + 4);
+        const uint32_t l[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+        way = 0;
+        uint32_t best = l[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w)
+            if (l[w] < best) {
+                best = l[w];
+                way = (uint32_t)w;
+            }
+        mark_range(a, a.lru_base + 8ull * set, 8, false);
+    }
+    const uint64_t slot = 8ull * set + way;
+    if (hit < 0) {
+        st_rlx_u64w(a.W + a.key_base + 2 * slot, r.key);
+        mark_range(a, a.key_base + 2 * slot, 2, true);
+    }
+    st_rlx_u64w(a.W + a.val_base + 2 * slot, r.value);
+    st_rlx32(a.W + a.lru_base + slot, (int32_t)stamp);
+    st_rlx32(a.W + verw, ld_rlx32(a.W + verw) + 1);
+    mark_range(a, a.val_base + 2 * slot, 2, true);
+    mark_range(a, a.lru_base + slot, 1, true);
+    mark_range(a, verw, 1, true);
+    out = way;
+}
+
+constexpr long long kPollCycles = 1000;  // ~0.5 us: one L2 round trip
+
+// Ordered phase: CTA segments of kSeg consecutive ranks, handed out in rank
+// order.  Thread t owns rank g*kSeg + t.  Each warp runs its 32 transactions
+// in waves: in one wave every lane whose inputs are all available executes
+// (lanes that are ready at the same time never depend on each other), then
+// the warp syncs.  Inputs come from a predecessor in the same warp (done in
+// an earlier wave, value in shared memory), in another warp of the segment
+// (shared-memory done flag), or in an earlier segment (the resource's packed
+// (turns done, value) word, polled once per wave, the load issued a wave
+// ahead so its latency overlaps the warp's work).  No lane ever spins while a
+// lane it waits for sits in the same warp.
+__global__ void __launch_bounds__(kSeg) k_seg_exec(OrderArgs o) {
+    // (segment + 1) << 32 | value: one aligned 8-byte store hands a word on
+    // to a later transaction of the segment, flag and data together
+    __shared__ unsigned long long s_pack[kSeg][4];
+    __shared__ uint32_t s_seg;
+    __shared__ int s_abort;
+    const ExecArgs &a = o.e;
+    const uint32_t n_ord = *o.n_ord;
+    const uint32_t n_seg = (n_ord + kSeg - 1) / kSeg;
+    const unsigned long long v0 = *o.v0;
+    const unsigned t = threadIdx.x;
+    const unsigned long long t0 = __shfl_sync(kFull, globaltimer_ns(), 0);
+    unsigned long long n_commit = 0, n_gaveup = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s_pack[t][k] = 0ull;
+    if (t == 0) s_abort = 0;
+    __syncthreads();
+    for (;;) {
+        if (t == 0) s_seg = s_abort ? 0xFFFFFFFFu : (uint32_t)atomicAdd(a.next, 1ull);
+        __syncthreads();
+        const uint32_t g = s_seg;
+        if (g >= n_seg) break;
+        const uint32_t r = g * kSeg + t;
+        OrdRec rc;
+        uint32_t n = 0, wl = 0;
+        if (r < n_ord) {
+            rc = o.rec[r];
+            n = rc.meta & 7u;
+            wl = (rc.meta >> 3) & 3u;
+        }
+        const bool cache = wl == HETM_WL_CACHE;
+        // output pointers now, so that no global load sits on the handoff path
+        uint64_t *o_order = nullptr;
+        uint8_t *o_status = nullptr;
+        void *o_out = nullptr;
+        const void *o_tx = nullptr;
+        if (n) {
+            const DevBatch &d = a.batches[rc.meta >> 16];
+            o_order = d.order;
+            o_status = d.status;
+            o_out = d.out;
+            o_tx = d.tx;
+        }
+        // W1 update naming 4 distinct words (the common case): slot j = word j
+        const bool rmw4 = wl == HETM_WL_RMW && n == 4 && ((rc.meta >> 8) & 0xFFu) == 0xE4u;
+        int32_t cur[4] = {0, 0, 0, 0};
+        int32_t nv[4] = {0, 0, 0, 0};
+        int32_t sum = 0;
+        uint32_t ext = 0, loc = 0;  // slots still waiting on an earlier segment / this segment
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k >= (int)n) continue;
+            const uint32_t tf = rc.turn[k];
+            if (!cache && (tf & kFLocal)) loc |= 1u << k;
+            else if (cache || (tf & kTurnMask)) ext |= 1u << k;
+            else cur[k] = ld_rlx32(a.W + rc.addr[k]);  // first access: launch-start value
+        }
+        unsigned long long pv[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (ext & (1u << k)) pv[k] = ld_rlx64(o.packed + rc.res[k]);
+        // Polls are paced per lane: a lane looks at its poll results (and
+        // polls again) only when its own back-off has expired, and the
+        // back-off grows with the number of turns still ahead of it, so lanes
+        // far from the front of the dependency chains rarely load the memory
+        // system.  Inside the wave loop only the work that a later
+        // transaction waits on is done (the shared-memory handoff and the
+        // publish to a later segment); everything else waits for the end.
+        long long next_check = clock64() + kPollCycles;
+        bool finished = n == 0;
+        bool executed = false;
+        bool timed_out = false;
+        uint32_t waves = 0;
+        uint32_t dist = 0;  // turns still to go before this lane's nearest external turn
+        for (;;) {
+            if (__all_sync(kFull, finished)) break;
+            bool ready = false;
+            if (!finished) {
+                if (ext) {
+                    const long long now = clock64();
+                    if (now >= next_check) {
+                        dist = 0xFFFFFFFFu;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (!(ext & (1u << k))) continue;
+                            const uint32_t c = (uint32_t)(pv[k] >> 32), need = rc.turn[k] & kTurnMask;
+                            if ((rc.turn[k] & kFWriter) ? c == need : c >= need) {
+                                ext &= ~(1u << k);
+                                cur[k] = (int32_t)(uint32_t)pv[k];
+                            } else {
+                                dist = min(dist, need > c ? need - c : 1u);
+                                pv[k] = ld_rlx64(o.packed + rc.res[k]);
+                            }
+                        }
+                        const uint32_t back = dist < 2048u ? dist * 32u : 65536u;
+                        next_check = now + kPollCycles + back;
+                        if (!ext) dist = 0;
+                    }
+                }
+                if (loc) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (!(loc & (1u << k))) continue;
+                        const unsigned long long pk =
+                            *(volatile unsigned long long *)&s_pack[rc.src[k] >> 2][rc.src[k] & 3u];
+                        if ((uint32_t)(pk >> 32) == g + 1) {
+                            cur[k] = (int32_t)(uint32_t)pk;
+                            loc &= ~(1u << k);
+                        }
+                    }
+                }
+                ready = (ext | loc) == 0;
+            }
+            if (ready && !cache) {
+                if (rmw4) {
+                    sum = cur[0] + cur[1] + cur[2] + cur[3];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) nv[k] = sum + k + (int32_t)rc.aux;
+                } else if (wl == HETM_WL_RMW) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t sl = (rc.meta >> (8 + 2 * j)) & 3u;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if ((uint32_t)k == sl) sum += cur[k];
+                    }
+                    // a word named twice keeps the value of its last position
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t sl = (rc.meta >> (8 + 2 * j)) & 3u;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if ((uint32_t)k == sl) nv[k] = sum + j + (int32_t)rc.aux;
+                    }
+                } else if (n == 1) {  // bank transfer onto the same account
+                    nv[0] = cur[0];
+                } else {
+                    nv[0] = cur[0] - (int32_t)rc.aux;
+                    nv[1] = cur[1] + (int32_t)rc.aux;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < (int)n)
+                        *(volatile unsigned long long *)&s_pack[t][k] =
+                            ((unsigned long long)(g + 1) << 32) | (uint32_t)nv[k];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < (int)n && (rc.turn[k] & kFPublish))
+                        st_rlx64(o.packed + rc.res[k],
+                                 ((unsigned long long)((rc.turn[k] & kTurnMask) + 1) << 32) |
+                                     (uint32_t)nv[k]);
+                finished = true;
+                executed = true;
+            } else if (ready) {  // cache request: holds or shares its set
+                const unsigned long long key = 2ull * (v0 + 1 + rc.u);
+                fence_gpu();  // acquire the set's previous holders' writes
+                const hetm_cache_req q = static_cast<const hetm_cache_req *>(o_tx)[rc.li];
+                uint64_t out = 0;
+                cache_request(a, q, (uint32_t)(key >> 1), out);
+                fence_gpu();  // release before handing the set on
+                atomicAdd(o.packed + rc.res[0], 1ull << 32);
+                if (o_out) static_cast<uint64_t *>(o_out)[rc.li] = out;
+                finished = true;
+                executed = true;
+            }
+            __syncwarp();
+            if (!__any_sync(kFull, ready)) {
+                if ((++waves & 15u) == 0 &&
+                    __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns) {
+                    timed_out = true;
+                    break;
+                }
+                // Idle warp: sleep in proportion to how far its nearest turn
+                // is, so that the warps at the front of the chains get the
+                // issue slots of the SM.
+                const uint32_t wd = __reduce_min_sync(kFull, finished ? 0xFFFFFFFFu : dist);
+                if (wd > 8 && wd != 0xFFFFFFFFu) __nanosleep(min(wd * 16u, 8000u));
+            }
+        }
+        if (executed) {
+            const unsigned long long key = 2ull * (v0 + 1 + rc.u);
+            if (!cache) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k >= (int)n) continue;
+                    if (rc.turn[k] & kFLast) st_rlx32(a.W + rc.addr[k], nv[k]);
+                    // the bitmaps are unions over the round: the word's first
+                    // writer marks it for all of its writers
+                    if ((rc.turn[k] & kTurnMask) == 0) mark_range(a, rc.addr[k], 1, true);
+                }
+                if (wl == HETM_WL_RMW && o_out) static_cast<int32_t *>(o_out)[rc.li] = sum;
+            }
+            if (o_order) o_order[rc.li] = key;
+            if (o_status) o_status[rc.li] = kCommitted;
+            ++n_commit;
+        }
+        if (timed_out && !finished) {
+            if (o_status) o_status[rc.li] = kGaveUp;
+            ++n_gaveup;
+            set_err(a.err, kErrTimeout);
+            s_abort = 1;
+            // release local successors so that they end too
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                *(volatile unsigned long long *)&s_pack[t][k] = (unsigned long long)(g + 1) << 32;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        n_commit += __shfl_xor_sync(kFull, n_commit, w);
+        n_gaveup += __shfl_xor_sync(kFull, n_gaveup, w);
+    }
+    if ((t & 31u) == 0) {
+        if (n_commit) atomicAdd(a.counters + 0, n_commit);
+        if (n_gaveup) atomicAdd(a.counters + 1, n_gaveup);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks,
+                           cudaStream_t s) {
+    k_ord_count<<<stream_blocks, 256, 0, s>>>(o);
+    const uint32_t scan_grid = (o.cap_tx + kScanTile - 1) / kScanTile;
+    cudaError_t e = device_scan<SumOp, true>(o.cnt, o.cnt, o.n_tx32, 0, scan_grid, o.scan_tot, 0, s);
+    if (e != cudaSuccess) return e;
+    k_ord_emit<<<stream_blocks, 256, 0, s>>>(o);
+    e = radix_sort(o.keys0, o.vals0, o.keys1, o.vals1, o.n_acc, o.cap_acc, o.key_bits, o.hist,
+                   o.scan_tot, s);
+    if (e != cudaSuccess) return e;
+    k_ord_runs<<<stream_blocks, 256, 0, s>>>(o);
+    const uint32_t acc_grid = (o.cap_acc + kScanTile - 1) / kScanTile;
+    e = device_scan<PairMaxOp, false>(o.runs, o.runs, o.n_acc, 0, acc_grid, o.scan_tot, 0, s);
+    if (e != cudaSuccess) return e;
+    k_ord_acc<<<stream_blocks, 256, 0, s>>>(o);
+    k_ord_ro<<<stream_blocks, 256, 0, s>>>(o);
+    e = cudaMemsetAsync(o.e.next, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_seg_exec<<<exec_blocks, kSeg, 0, s>>>(o);
+    return cudaGetLastError();
+}
+
+int ordered_exec_occupancy(int *blocks_per_sm) {
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec, kSeg, 0);
+}
+
+}  // namespace hetm

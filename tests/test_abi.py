@@ -32,6 +32,7 @@ def test_strerror_and_defaults_without_gpu():
     cfg = h.hetm_config_default()
     assert cfg.ws_chunk_bytes == 16384 and cfg.log_chunk_bytes == 49152
     assert cfg.lock_log2 == 22 and cfg.max_batches == 4096
+    assert cfg.exec_mode == h.HETM_EXEC_ORDERED and cfg.max_round_tx == 1 << 22
 
 
 def test_record_layouts_match_workloads():
@@ -39,7 +40,7 @@ def test_record_layouts_match_workloads():
     import workloads as wl
     assert h.LOG_DTYPE == wl.LOG_DTYPE
     assert ctypes.sizeof(h.hetm_batch) == 48
-    assert ctypes.sizeof(h.hetm_config) == 112
+    assert ctypes.sizeof(h.hetm_config) == 128
 
 
 def test_init_rejects_bad_arguments_before_touching_the_device():

@@ -20,6 +20,13 @@ from roundkit import bits_of, check_keys, flags_of, gpu_bitmaps, submit, to_dev
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+#: both GPU guest TMs: 0 = ordered (default), 1 = optimistic STM
+MODES = [0, 1]
+
+
+def cfg(mode, **kw):
+    kw["exec_mode"] = mode
+    return kw
 
 
 @pytest.fixture(scope="module")
@@ -107,9 +114,10 @@ def _finish_round(ctx, h, torch, start, replayed, R, log, G, ts_state=None, ship
 
 
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("name", ["bank_no_conflict.json", "bank_conflict.json",
                                   "granule_false_sharing.json"])
-def test_golden_bank_on_gpu(hetm, torch, name):
+def test_golden_bank_on_gpu(hetm, torch, name, mode):
     """Hand-enumerated bank rounds (Sec. IV-C) through the CUDA path."""
     g = json.load(open(os.path.join(GOLDEN, name)))
     h = hetm
@@ -119,7 +127,7 @@ def test_golden_bank_on_gpu(hetm, torch, name):
         tx[i] = tuple(r)
     keep = np.array(g["status"]) == 1
     tx = tx[keep]
-    with h.Context(len(start), g["granule_bytes"], {"ws_chunk_bytes": 16, "lock_log2": 4}) as ctx:
+    with h.Context(len(start), g["granule_bytes"], cfg(mode, ws_chunk_bytes=16, lock_log2=4)) as ctx:
         ctx.load(start)
         b = submit(ctx, torch, wl.WORKLOAD_BANK, tx)
         replayed, R, D, _, _ = _exec_and_check_replay(ctx, h, torch, start, [(tx, b, 0)],
@@ -130,12 +138,13 @@ def test_golden_bank_on_gpu(hetm, torch, name):
         assert ref.flags.tolist() == g["expect"]["flags"]
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("partitioned", [False, True])
-def test_bank_config_round(hetm, torch, partitioned):
+def test_bank_config_round(hetm, torch, partitioned, mode):
     """Bank: 2^20 accounts, 65,536 GPU transfers, 4 x 10,000 CPU transfers, G = 4 B, seed 0."""
     h = hetm
     b = wl.bank_round(seed=0, partitioned=partitioned)
-    with h.Context(b.n_accounts, 4) as ctx:
+    with h.Context(b.n_accounts, 4, cfg(mode)) as ctx:
         ctx.load(b.init)
         bo = submit(ctx, torch, wl.WORKLOAD_BANK, b.gpu_tx)
         replayed, R, D, keys, stat = _exec_and_check_replay(ctx, h, torch, b.init,
@@ -148,15 +157,16 @@ def test_bank_config_round(hetm, torch, partitioned):
         assert oracle.sum64(ref.final) == oracle.sum64(b.init)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("uniform", [False, True])
-def test_rmw_round(hetm, torch, uniform):
+def test_rmw_round(hetm, torch, uniform, mode):
     """W1-style transactions, Zipf(0.99) or uniform, 10% updates: replay parity + round."""
     h = hetm
     log2w, G = 16, 64
     start = wl.init_words(5, 0, 1 << log2w)
     tx = wl.rmw_batch(seed=5, batch=0, n_tx=30000, log2_words=log2w, uniform=uniform)
     log = wl.cpu_write_log(5, 0, 3000, log2w, cpu_threads=1, uniform=uniform)[0]
-    with h.Context(1 << log2w, G, {"ws_chunk_bytes": 1024}) as ctx:
+    with h.Context(1 << log2w, G, cfg(mode, ws_chunk_bytes=1024)) as ctx:
         ctx.load(start)
         bo = submit(ctx, torch, wl.WORKLOAD_RMW, tx, txid_base=7)
         replayed, R, D, keys, stat = _exec_and_check_replay(ctx, h, torch, start,
@@ -165,7 +175,8 @@ def test_rmw_round(hetm, torch, uniform):
         _finish_round(ctx, h, torch, start, replayed, R, log, G)
 
 
-def test_rmw_uneven_batches_one_launch_and_per_batch(hetm, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_rmw_uneven_batches_one_launch_and_per_batch(hetm, torch, mode):
     """Many uneven batches drained by one persistent launch, and one launch per batch."""
     h = hetm
     log2w, G = 15, 4
@@ -173,7 +184,7 @@ def test_rmw_uneven_batches_one_launch_and_per_batch(hetm, torch):
     sizes = [1, 31, 32, 33, 1000, 4097, 77, 12000]
     txs = [wl.rmw_batch(seed=9, batch=i, n_tx=n, log2_words=log2w) for i, n in enumerate(sizes)]
     for per_batch in (False, True):
-        with h.Context(1 << log2w, G, {"ws_chunk_bytes": 64}) as ctx:
+        with h.Context(1 << log2w, G, cfg(mode, ws_chunk_bytes=64)) as ctx:
             ctx.load(start)
             bases = np.cumsum([0] + sizes[:-1])
             batches = [(t, submit(ctx, torch, wl.WORKLOAD_RMW, t, txid_base=int(bb)), int(bb))
@@ -215,14 +226,15 @@ def test_log_shipped_by_concurrent_threads(hetm, torch):
                       ship_threads=4)
 
 
-def test_rounds_chain_with_graph(hetm, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_rounds_chain_with_graph(hetm, torch, mode):
     """Five whole rounds through hetm_round (captured graphs), TS carried across rounds."""
     h = hetm
     log2w, G = 16, 64
     n = 1 << log2w
     state = wl.init_words(3, 0, n)
     ts_state = np.zeros(n, np.uint32)
-    with h.Context(n, G, {"cpu_threads": 2, "ws_chunk_bytes": 256}) as ctx:
+    with h.Context(n, G, cfg(mode, cpu_threads=2, ws_chunk_bytes=256)) as ctx:
         ctx.load(state)
         for r in range(5):
             uniform = r % 2 == 1
@@ -248,7 +260,8 @@ def test_rounds_chain_with_graph(hetm, torch):
             state = ref.final
 
 
-def test_cache_round(hetm, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_cache_round(hetm, torch, mode):
     """Object cache (Sec. V-D): GET/PUT replay parity, outputs, bitmaps, CPU PUT conflicts."""
     h = hetm
     lay = wl.CacheLayout(log2_sets=12)
@@ -256,7 +269,7 @@ def test_cache_round(hetm, torch):
     start = wl.cache_prefill(lay, 1 << 15)
     cfg = {"lock_shift": 4, "cache_log2_sets": lay.log2_sets, "cache_key_base": lay.key_base,
            "cache_val_base": lay.val_base, "cache_lru_base": lay.gpu_lru_base,
-           "cache_ver_base": lay.ver_base, "ws_chunk_bytes": 64}
+           "cache_ver_base": lay.ver_base, "ws_chunk_bytes": 64, "exec_mode": mode}
     reqs = wl.cache_batch(seed=4, batch=0, n_req=40000, n_keys=n_keys)
     with h.Context(lay.n_words, 64, cfg) as ctx:
         ctx.load(start)
@@ -293,14 +306,15 @@ def test_validate_only_leaves_state(hetm, torch):
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_W), v.init)
 
 
-def test_whole_stmr_granule_conflicts(hetm, torch):
+@pytest.mark.parametrize("mode", MODES)
+def test_whole_stmr_granule_conflicts(hetm, torch, mode):
     """Granule = whole STMR: any GPU access + any CPU write conflicts."""
     h = hetm
     n = 4096
     start = np.arange(n, dtype=np.int32)
     tx = wl.rmw_batch(seed=8, batch=0, n_tx=100, log2_words=12, uniform=True)
     log = _log([(5, 1, 1)])
-    with h.Context(n, 4 * n, {"ws_chunk_bytes": 4 * n}) as ctx:
+    with h.Context(n, 4 * n, cfg(mode, ws_chunk_bytes=4 * n)) as ctx:
         ctx.load(start)
         bo = submit(ctx, torch, wl.WORKLOAD_RMW, tx)
         replayed, R, D, _, _ = _exec_and_check_replay(ctx, h, torch, start, [(tx, bo, 0)], 4 * n,
