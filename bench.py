@@ -257,6 +257,66 @@ def bench_validation(torch, h, reps=20):
 
 
 # ---------------------------------------------------------------------------
+# serving: Poisson arrivals of bank / object-cache batches, fused vs per-batch
+# ---------------------------------------------------------------------------
+SERVE_SETS_LOG2 = 22
+SERVE_BANK_LOG2 = 26
+SERVE_RATE = 200.0
+
+
+def serving_inputs(n_batches, seed=4):
+    lay = wl.CacheLayout(SERVE_SETS_LOG2)
+    bank_base = (lay.n_words + 15) // 16 * 16
+    n_words = bank_base + (1 << SERVE_BANK_LOG2)
+    init = np.zeros(n_words, np.int32)
+    init[:lay.n_words] = wl.cache_prefill(lay, 1 << 25)
+    init[bank_base:] = 1000
+    arrive = wl.poisson_arrivals(seed, n_batches, SERVE_RATE)
+    sizes = wl.log_uniform_sizes(seed, wl.S.SIZE, n_batches, 1 << 10, 1 << 20)
+    kinds = (wl.uniform01(wl.draws_range(seed, wl.S.KIND, n_batches)) < 0.5)
+    batches = []
+    for i in range(n_batches):
+        if kinds[i]:
+            tx = wl.bank_transfers(seed * 1000 + i, (wl.S.SRC, wl.S.DST, wl.S.AMT), int(sizes[i]),
+                                   0, 1 << SERVE_BANK_LOG2)
+            batches.append((1, tx))
+        else:
+            batches.append((3, wl.cache_batch(seed, i, int(sizes[i]), 1 << 26)))
+    cfg = {"cache_log2_sets": SERVE_SETS_LOG2, "cache_key_base": lay.key_base,
+           "cache_val_base": lay.val_base, "cache_lru_base": lay.gpu_lru_base,
+           "cache_ver_base": lay.ver_base, "lock_shift": 4, "cpu_threads": 1}
+    return init, arrive, batches, bank_base, cfg
+
+
+def bench_serving(torch, h, inputs, per_batch):
+    init, arrive, batches, bank_base, cfg = inputs
+    with h.Context(len(init), GRANULE, cfg) as ctx:
+        ctx.load(init)
+        with h.Server(ctx, per_batch=per_batch) as srv:
+            # warm-up: one small batch of each kind
+            warm_bank = wl.bank_transfers(9, (wl.S.SRC, wl.S.DST, wl.S.AMT), 1024, 0,
+                                          1 << SERVE_BANK_LOG2)
+            for wk, tx in ((1, warm_bank), (3, wl.cache_batch(9, 0, 1024, 1 << 26))):
+                srv.wait(srv.submit(wk, tx, word_base=bank_base if wk == 1 else 0))
+            srv0 = srv.stats()
+            ids = []
+            t0 = time.perf_counter()
+            for i, (wk, tx) in enumerate(batches):
+                delay = arrive[i] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                ids.append(srv.submit(wk, tx, word_base=bank_base if wk == 1 else 0))
+            lat = [srv.wait(b) for b in ids]
+            st = srv.stats()
+        n_tx = sum(len(tx) for _, tx in batches)
+        span = max(1e-9, (time.perf_counter() - t0))
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "tx_per_s": (st["committed"] - srv0["committed"]) / span, "n_tx": n_tx,
+            "rounds": st["rounds"] - srv0["rounds"], "batches": len(batches),
+            "span_s": span}
+
+
+# ---------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
 def oracle_sample(inputs, frac_tx=1 / 4):
@@ -296,6 +356,7 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--serve-batches", type=int, default=300)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -345,6 +406,13 @@ def main():
         e2e_s, e2e_commit = res["e2e_s"], res["e2e_commit"]
     if rank != 0:
         return
+    import paper_1905_00661_b300 as h
+    sv_in = serving_inputs(args.serve_batches)
+    serving = {"fused": bench_serving(torch, h, sv_in, False),
+               "per_batch": bench_serving(torch, h, sv_in, True),
+               "workload": f"serving_poisson{SERVE_RATE:.0f}/s_bank2^{SERVE_BANK_LOG2}_cache2^{SERVE_SETS_LOG2}sets_1K-1M",
+               "batches": args.serve_batches}
+    del sv_in
     cpu = oracle_sample(inputs, 1 / 4)
     K = args.steps
     exec_ms = float(np.mean(res["exec_ms"]))
@@ -373,6 +441,7 @@ def main():
         "e2e": {"value": e2e_commit / e2e_s, "unit": "tx/s",
                 "h2d_bytes_per_step": N_TX * 20 + N_LOG * 12,
                 "d2h_bytes_per_step": N_TX * (8 + 1 + 4)},
+        "serving": serving,
         "gpu_launches": 4 * K,
         "clocks": res["clocks"],
         "cpu_baseline": {"value": cpu["value"], "unit": "tx/s", "cores": 1, "kind": "oracle",

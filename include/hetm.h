@@ -178,6 +178,9 @@ HETM_API int hetm_bitmap_words(hetm_ctx *ctx, uint64_t *rs_words, uint64_t *ws_w
 /* Wait for all work queued on the context stream. */
 HETM_API int hetm_sync(hetm_ctx *ctx);
 
+/* The cudaStream_t all device work of the context runs on. */
+HETM_API void *hetm_ctx_stream(hetm_ctx *ctx);
+
 /* -------------------------------------------------- execution phase (A1) */
 /* One transaction batch.  All pointers are device pointers; outputs may be
  * NULL.  order[i] is the commit key of transaction i: sorting the committed
@@ -303,6 +306,57 @@ typedef struct hetm_round_stats {
  * captured on first use and replayed.  stats NULL = asynchronous (no host
  * synchronization); otherwise waits and fills *stats. */
 HETM_API int hetm_round(hetm_ctx *ctx, hetm_round_stats *stats);
+
+/* Wait for the round last launched by hetm_round(ctx, NULL) and fill *stats
+ * (may be NULL).  Returns the round's status like hetm_round. */
+HETM_API int hetm_round_wait(hetm_ctx *ctx, hetm_round_stats *stats);
+
+/* ---------------------------------------------------------- serving (A7) */
+/* A serving loop over one context: client threads submit transaction
+ * batches (host records) at any time; one loop thread admits waiting
+ * batches in arrival order while the device-memory budget and the round's
+ * capacity allow, stages their records on the device while the previous
+ * round still runs, and executes all admitted batches in one round (one
+ * persistent executor launch over uneven batches, then validation, apply,
+ * merge; Sec. IV-C) -- or one round per batch with per_batch = 1.  A batch
+ * completes when its round is merged and its results are in the caller's
+ * host buffers; its commit latency runs from submit to that point.  While a
+ * server exists, only it drives the context (hetm_cpu_log_write stays open
+ * to CPU threads). */
+typedef struct hetm_request {
+    uint32_t workload, n_tx;
+    const void *host_tx;     /* n_tx records (host; read during admission)   */
+    uint64_t *host_order;    /* out (host, may be NULL): commit keys          */
+    uint8_t *host_status;    /* out (host, may be NULL): 1 committed          */
+    void *host_out;          /* out (host, may be NULL): RMW int32 / cache u64 */
+    uint32_t txid_base, word_base;
+} hetm_request;
+
+typedef struct hetm_server_config {
+    int32_t per_batch;           /* 1: one round per batch (the plain form)        */
+    uint32_t max_round_batches;  /* batches per round; 1024                        */
+    uint64_t max_round_tx;       /* transactions per round; 1<<22                  */
+    uint64_t device_budget;      /* bytes for in-flight batches; 0 = half of free  */
+} hetm_server_config;
+
+typedef struct hetm_server_stats {
+    uint64_t rounds, completed, committed, refused;
+    double p50_ms, p99_ms, max_ms;  /* commit latency of completed batches   */
+    double span_s;                  /* first submit to last completion        */
+} hetm_server_stats;
+
+typedef struct hetm_server hetm_server;
+HETM_API int hetm_server_config_default(hetm_server_config *cfg);
+/* Start the loop thread.  The context must outlive the server. */
+HETM_API int hetm_server_create(hetm_server **out, hetm_ctx *ctx, const hetm_server_config *cfg);
+/* Queue a batch (thread-safe).  HETM_EBUSY if it can never fit the budget
+ * or the round capacity.  The host buffers must stay valid until wait. */
+HETM_API int hetm_server_submit(hetm_server *s, const hetm_request *r, uint64_t *id);
+/* Block until batch `id` completed (bounded: HETM_ETIMEOUT after 120 s). */
+HETM_API int hetm_server_wait(hetm_server *s, uint64_t id, double *latency_ms);
+HETM_API int hetm_server_get_stats(hetm_server *s, hetm_server_stats *out);
+/* Drain the queue, stop the loop thread, free the server. */
+HETM_API void hetm_server_destroy(hetm_server *s);
 
 #ifdef __cplusplus
 }

@@ -66,7 +66,29 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_read_stmr", "hetm_device_ptr", "hetm_bitmap_words", "hetm_sync",
            "hetm_gpu_submit_batch", "hetm_gpu_exec", "hetm_exec_counters", "hetm_gpu_mark",
            "hetm_cpu_log_write", "hetm_log_attach", "hetm_validate", "hetm_validate_only",
-           "hetm_merge", "hetm_round", "hetm_validate_noalloc")
+           "hetm_merge", "hetm_round", "hetm_validate_noalloc", "hetm_ctx_stream",
+           "hetm_round_wait", "hetm_server_config_default", "hetm_server_create",
+           "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
+           "hetm_server_destroy")
+
+
+class hetm_request(ctypes.Structure):
+    _fields_ = [("workload", _u32), ("n_tx", _u32), ("host_tx", _vp), ("host_order", _vp),
+                ("host_status", _vp), ("host_out", _vp), ("txid_base", _u32), ("word_base", _u32)]
+
+
+class hetm_server_config(ctypes.Structure):
+    _fields_ = [("per_batch", _i32), ("max_round_batches", _u32), ("max_round_tx", _u64),
+                ("device_budget", _u64)]
+
+
+class hetm_server_stats(ctypes.Structure):
+    _fields_ = [("rounds", _u64), ("completed", _u64), ("committed", _u64), ("refused", _u64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("span_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class HetmError(RuntimeError):
@@ -98,6 +120,14 @@ def _declare(L):
         "hetm_merge": (_int, [_vp, _int]),
         "hetm_round": (_int, [_vp, P(hetm_round_stats)]),
         "hetm_validate_noalloc": (_int, [_vp, _u64, _vp, _u32, _u64, _vp, _vp, _vp, _vp]),
+        "hetm_ctx_stream": (_vp, [_vp]),
+        "hetm_round_wait": (_int, [_vp, P(hetm_round_stats)]),
+        "hetm_server_config_default": (_int, [P(hetm_server_config)]),
+        "hetm_server_create": (_int, [P(_vp), _vp, P(hetm_server_config)]),
+        "hetm_server_submit": (_int, [_vp, P(hetm_request), P(_u64)]),
+        "hetm_server_wait": (_int, [_vp, _u64, P(ctypes.c_double)]),
+        "hetm_server_get_stats": (_int, [_vp, P(hetm_server_stats)]),
+        "hetm_server_destroy": (None, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -336,3 +366,57 @@ class Context:
         _ck(_lib.hetm_round(self.h, None), "hetm_round")
         self._leave()
         return None
+
+
+class Server:
+    """Serving loop over a Context (continuous batching into rounds, see include/hetm.h).
+
+    ``submit`` takes numpy record arrays and fills numpy result arrays that the
+    caller keeps alive until ``wait``; ``per_batch`` selects one round per batch."""
+
+    def __init__(self, ctx: Context, per_batch=False, max_round_batches=1024,
+                 max_round_tx=1 << 22, device_budget=0):
+        cfg = hetm_server_config()
+        _ck(_lib.hetm_server_config_default(ctypes.byref(cfg)), "hetm_server_config_default")
+        cfg.per_batch = int(per_batch)
+        cfg.max_round_batches = max_round_batches
+        cfg.max_round_tx = max_round_tx
+        cfg.device_budget = device_budget
+        self.ctx = ctx
+        self.h = _vp()
+        ctx.torch.cuda.synchronize()
+        _ck(_lib.hetm_server_create(ctypes.byref(self.h), ctx.h, ctypes.byref(cfg)),
+            "hetm_server_create")
+        self._keep = {}
+
+    def submit(self, workload, tx, order=None, status=None, out=None, txid_base=0, word_base=0):
+        tx = np.ascontiguousarray(tx)
+        r = hetm_request(workload, len(tx), tx.ctypes.data, _ptr(order), _ptr(status), _ptr(out),
+                         txid_base, word_base)
+        bid = _u64()
+        _ck(_lib.hetm_server_submit(self.h, ctypes.byref(r), ctypes.byref(bid)), "hetm_server_submit")
+        self._keep[bid.value] = (tx, order, status, out)
+        return bid.value
+
+    def wait(self, bid):
+        lat = ctypes.c_double()
+        rc = _lib.hetm_server_wait(self.h, bid, ctypes.byref(lat))
+        self._keep.pop(bid, None)
+        _ck(rc, "hetm_server_wait")
+        return lat.value
+
+    def stats(self):
+        st = hetm_server_stats()
+        _ck(_lib.hetm_server_get_stats(self.h, ctypes.byref(st)), "hetm_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.hetm_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -115,6 +115,10 @@ struct hetm_ctx {
     unsigned long long prev_counters[3] = {0, 0, 0};
 
     std::vector<void *> dev_allocs;
+    // the last round launched by hetm_round (read back by hetm_round_wait)
+    uint64_t last_n_log = 0;
+    uint32_t last_nb = 0;
+    bool round_open = false;
 };
 
 #define CK(x)                                                                       \
@@ -591,6 +595,8 @@ int hetm_bitmap_words(hetm_ctx *c, uint64_t *rs_words, uint64_t *ws_words) {
     return HETM_OK;
 }
 
+void *hetm_ctx_stream(hetm_ctx *c) { return c ? static_cast<void *>(c->stream) : nullptr; }
+
 int hetm_sync(hetm_ctx *c) {
     if (!c) return HETM_EINVAL;
     CK(cudaStreamSynchronize(c->ship));
@@ -605,8 +611,10 @@ int hetm_gpu_submit_batch(hetm_ctx *c, const hetm_batch *b, uint64_t *batch_id) 
     if (b->workload == HETM_WL_CACHE) {
         const hetm_config &f = c->cfg;
         const uint64_t ns = 1ull << f.cache_log2_sets;
-        // one lock stripe per set region: needs >= 16-word stripes, aligned regions
-        if (f.lock_shift < 4 || f.cache_key_base % 16 || f.cache_val_base % 16 ||
+        // aligned regions (16-byte vector loads of a set's keys and stamps); the
+        // optimistic executor also needs one lock stripe per set region
+        if ((f.exec_mode == HETM_EXEC_OPTIMISTIC && f.lock_shift < 4) ||
+            f.cache_key_base % 16 || f.cache_val_base % 16 ||
             f.cache_lru_base % 16 || f.cache_key_base + 16 * ns > c->n_words ||
             f.cache_val_base + 16 * ns > c->n_words || f.cache_lru_base + 8 * ns > c->n_words ||
             f.cache_ver_base + ns > c->n_words)
@@ -770,8 +778,25 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
     CK(cudaGraphLaunch(c->g_sync, c->stream));
     CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
     CK(cudaEventRecord(c->ev[5], c->stream));
+    c->last_n_log = n;
+    c->last_nb = nb;
+    c->round_open = true;
     if (!stats) return HETM_OK;
+    return hetm_round_wait(c, stats);
+}
+
+int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
+    if (!c) return HETM_EINVAL;
     CK(cudaEventSynchronize(c->ev[5]));
+    if (!c->round_open) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return HETM_OK;
+    }
+    c->round_open = false;
+    const uint64_t n = c->last_n_log;
+    const uint32_t nb = c->last_nb;
+    hetm_round_stats local;
+    if (!stats) stats = &local;
     std::memset(stats, 0, sizeof(*stats));
     stats->n_log = n;
     stats->n_conflicts = c->out->conflicts;
