@@ -288,8 +288,9 @@ def serving_inputs(n_batches, seed=4):
     return init, arrive, batches, bank_base, cfg
 
 
-def bench_serving(torch, h, inputs, per_batch):
+def bench_serving(torch, h, inputs, per_batch, rate=SERVE_RATE):
     init, arrive, batches, bank_base, cfg = inputs
+    arrive = arrive * (SERVE_RATE / rate)  # the same Poisson pattern at another rate
     with h.Context(len(init), GRANULE, cfg) as ctx:
         ctx.load(init)
         with h.Server(ctx, per_batch=per_batch) as srv:
@@ -310,7 +311,7 @@ def bench_serving(torch, h, inputs, per_batch):
             st = srv.stats()
         n_tx = sum(len(tx) for _, tx in batches)
         span = max(1e-9, (time.perf_counter() - t0))
-    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+    return {"rate": rate, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "tx_per_s": (st["committed"] - srv0["committed"]) / span, "n_tx": n_tx,
             "rounds": st["rounds"] - srv0["rounds"], "batches": len(batches),
             "span_s": span}
@@ -408,10 +409,11 @@ def main():
         return
     import paper_1905_00661_b300 as h
     sv_in = serving_inputs(args.serve_batches)
-    serving = {"fused": bench_serving(torch, h, sv_in, False),
-               "per_batch": bench_serving(torch, h, sv_in, True),
-               "workload": f"serving_poisson{SERVE_RATE:.0f}/s_bank2^{SERVE_BANK_LOG2}_cache2^{SERVE_SETS_LOG2}sets_1K-1M",
-               "batches": args.serve_batches}
+    rates = [SERVE_RATE, 5 * SERVE_RATE, 25 * SERVE_RATE]
+    serving = {"fused": [bench_serving(torch, h, sv_in, False, r) for r in rates],
+               "per_batch": [bench_serving(torch, h, sv_in, True, r) for r in rates],
+               "workload": f"serving_poisson_bank2^{SERVE_BANK_LOG2}_cache2^{SERVE_SETS_LOG2}sets_1K-1M",
+               "rates_per_s": rates, "batches": args.serve_batches}
     del sv_in
     cpu = oracle_sample(inputs, 1 / 4)
     K = args.steps

@@ -168,7 +168,14 @@ __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_
 // Merge (Sec. IV-C Merge Phase, Sec. IV-D): every WS_bmp chunk is copied
 // W -> S when validation succeeded (the GPU's speculative commits become
 // final) or S -> W when it failed (the GPU batch is undone; S already holds
-// start + CPU writes).  A warp moves 2 KiB per step, 4 vectors per lane.
+// start + CPU writes).  Warps walk the chunks: a clean chunk costs one
+// (cached) bitmap load, so the cost follows the dirty bytes; a dirty chunk
+// is copied with 16-byte vectors, 4 in flight per lane.  Chunks smaller
+// than a warp's 32 vectors are packed several to a warp.
+__device__ __forceinline__ bool chunk_dirty(const uint32_t *ws, uint64_t c) {
+    return (__ldg(ws + (c >> 5)) >> (c & 31)) & 1u;
+}
+
 __global__ void __launch_bounds__(256) k_merge(const uint32_t *__restrict__ ws, uint32_t cshift,
                                                int32_t *W, int32_t *S, uint64_t n_words,
                                                const unsigned long long *conflicts, int force,
@@ -181,26 +188,36 @@ __global__ void __launch_bounds__(256) k_merge(const uint32_t *__restrict__ ws, 
     const uint64_t n_threads = gridDim.x * (uint64_t)blockDim.x;
     const uint64_t warp = tid >> 5, n_warps = n_threads >> 5;
     const uint64_t n_vec = n_words / 4;
-    const uint64_t n_spans = (n_vec + 127) / 128;
-    for (uint64_t sp = warp; sp < n_spans; sp += n_warps) {
-        uint4 r[4];
-        bool d[4];
+    const uint64_t wpc = 1ull << cshift;              // words per chunk (>= 4)
+    const uint64_t vpc = wpc / 4;                     // vectors per chunk
+    const uint64_t n_chunks = (n_words + wpc - 1) / wpc;
+    if (vpc >= 32) {
+        for (uint64_t c = warp; c < n_chunks; c += n_warps) {
+            if (!chunk_dirty(ws, c)) continue;
+            const uint64_t v0 = c * vpc;
+            const uint64_t v1 = v0 + vpc < n_vec ? v0 + vpc : n_vec;
+            for (uint64_t v = v0 + lane; v < v1; v += 128) {
+                uint4 r[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint64_t v = sp * 128 + lane + 32u * k;
-            uint64_t ch = (v * 4) >> cshift;
-            d[k] = v < n_vec && ((__ldg(ws + (ch >> 5)) >> (ch & 31)) & 1u);
-            if (d[k]) r[k] = __ldcs(src + v);
+                for (int k = 0; k < 4; ++k)
+                    if (v + 32u * k < v1) r[k] = __ldcs(src + v + 32u * k);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (v + 32u * k < v1) __stcs(dst + v + 32u * k, r[k]);
+            }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (d[k]) __stcs(dst + sp * 128 + lane + 32u * k, r[k]);
+    } else {
+        const uint64_t per = 32 / vpc;  // chunks per warp step
+        for (uint64_t c0 = warp * per; c0 < n_chunks; c0 += n_warps * per) {
+            const uint64_t c = c0 + lane / vpc;
+            const uint64_t v = c * vpc + lane % vpc;
+            if (c < n_chunks && v < n_vec && chunk_dirty(ws, c)) __stcs(dst + v, __ldcs(src + v));
+        }
     }
     // the last n_words % 4 words
     if (tid == 0) {
         for (uint64_t w = n_vec * 4; w < n_words; ++w) {
-            uint64_t ch = w >> cshift;
-            if ((ws[ch >> 5] >> (ch & 31)) & 1u) {
+            if (chunk_dirty(ws, w >> cshift)) {
                 int32_t *d = conflict ? W : S;
                 const int32_t *s = conflict ? S : W;
                 d[w] = s[w];
@@ -208,13 +225,12 @@ __global__ void __launch_bounds__(256) k_merge(const uint32_t *__restrict__ ws, 
         }
     }
     if (dirty_count) {
-        const uint64_t n_chunks = ((n_words - 1) >> cshift) + 1;
         const uint64_t n_ws = (n_chunks + 31) / 32;
-        unsigned long long c = 0;
-        for (uint64_t i = tid; i < n_ws; i += n_threads) c += __popc(ws[i]);
+        unsigned long long cnt = 0;
+        for (uint64_t i = tid; i < n_ws; i += n_threads) cnt += __popc(ws[i]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-        if (lane == 0 && c) atomicAdd(dirty_count, c);
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(dirty_count, cnt);
     }
 }
 
