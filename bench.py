@@ -351,6 +351,43 @@ def config_dict(world):
             "parallelism": f"replicas{world}" if world > 1 else "single"}
 
 
+def run_case(name):
+    """Small single-shot cases used for ncu captures (a few GB on the device)."""
+    import torch
+
+    import paper_1905_00661_b300 as h
+    if name == "rmw_small":  # one Zipf(0.99) W1 round: 2^26 words, 1M transactions
+        log2w = 26
+        init = wl.init_stmr(SEED, 1 << log2w)
+        tx = wl.rmw_batch(seed=SEED, batch=0, n_tx=1 << 20, log2_words=log2w)
+        with h.Context(1 << log2w, GRANULE, {"cpu_threads": 4, "max_round_tx": 1 << 20}) as ctx:
+            ctx.load(init)
+            dtx = torch.from_numpy(tx.view(np.uint8)).cuda()
+            o = torch.empty(len(tx), dtype=torch.int64, device="cuda")
+            st_ = torch.empty(len(tx), dtype=torch.uint8, device="cuda")
+            out = torch.empty(len(tx), dtype=torch.int32, device="cuda")
+            ctx.submit_batch(h.HETM_WL_RMW, dtx, o, st_, out, n_tx=len(tx))
+            st = ctx.round(stats=True)
+        print(json.dumps({"case": name, "committed": st["committed"], "ms_exec": st["ms_exec"],
+                          "rc": st["rc"]}))
+        return st["rc"]
+    if name == "validate_small":  # validation-at-scale log (16M tuples) on a 2^27-word STMR
+        v = wl.validation_round(seed=1, log2_words=27, granule_bytes=32, with_init=False)
+        with h.Context(1 << 27, 32, {"log_capacity": 1 << 12, "exec_mode": 1}) as ctx:
+            first = (v.read_granules.astype(np.uint64) * 8).astype(np.uint32)
+            ctx.gpu_mark(torch.from_numpy(first).cuda())
+            dlog = torch.from_numpy(v.log.view(np.uint8)).cuda()
+            flags = torch.zeros((len(v.log) + 31) // 32, dtype=torch.int32, device="cuda")
+            cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+            for _ in range(3):
+                cnt.zero_()
+                ctx.validate_only(dlog, len(v.log), flags, cnt)
+            torch.cuda.synchronize()
+        print(json.dumps({"case": name, "hits": int(cnt.item()), "expected": v.n_hits_planted}))
+        return 0 if int(cnt.item()) == v.n_hits_planted else 1
+    raise SystemExit(f"unknown case {name}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,7 +395,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--serve-batches", type=int, default=300)
+    ap.add_argument("--case", default=None, help="run one small profiling case and exit")
     args = ap.parse_args()
+    if args.case:
+        raise SystemExit(run_case(args.case))
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

@@ -73,6 +73,7 @@ struct hetm_ctx {
 
     int32_t *W = nullptr, *S = nullptr;
     uint32_t *TS = nullptr, *rs = nullptr, *ws = nullptr;
+    uint32_t *filter = nullptr;    // shared-memory filter of RS_bmp (validation)
     unsigned long long *locks = nullptr;
     Scratch *scr = nullptr;
     DevRound *d_round = nullptr;   // [0] fused round, [1 + b] batch b alone
@@ -263,6 +264,7 @@ ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
     a.lock_shift = c->cfg.lock_shift;
     a.gv = &c->scr->gv;
     a.rs = c->rs;
+    a.filter = c->filter;
     a.gshift = c->gshift;
     a.ws = c->ws;
     a.cshift = c->cshift;
@@ -318,13 +320,14 @@ int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e) {
     CK(cudaMemsetAsync(&c->scr->conflicts, 0, 2 * sizeof(unsigned long long), c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[0], c->stream, cudaEventRecordExternal));
     CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, flags, &c->scr->conflicts, c->TS,
-                       &c->scr->err, c->stream_blocks, c->stream));
+                       &c->scr->err, c->filter, c->n_sm, c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
     CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[2], c->stream, cudaEventRecordExternal));
     CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, force,
                     &c->scr->dirty, c->stream_blocks, c->stream));
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
+    CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal));
     CK(cudaMemcpyAsync(c->out, c->scr->counters, sizeof(RoundOut) - sizeof(int) * 2,
@@ -470,6 +473,7 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
     if (!dev_alloc_t(c, &c->W, stmr_words) || !dev_alloc_t(c, &c->S, stmr_words) ||
         !dev_alloc_t(c, &c->TS, stmr_words) || !dev_alloc_t(c, &c->rs, c->rs_words) ||
         !dev_alloc_t(c, &c->ws, c->ws_words) || !dev_alloc_t(c, &c->locks, 1ull << d.lock_log2) ||
+        !dev_alloc_t(c, &c->filter, kFilterBits / 32) ||
         !dev_alloc_t(c, &c->scr, 1) || !dev_alloc_t(c, &c->d_round, nb + 1) ||
         !dev_alloc_t(c, &c->d_batches, nb) || !dev_alloc_t(c, &c->d_prefix, nb + 1) ||
         !dev_alloc_t(c, &c->d_prefix0, 2) || !dev_alloc_t(c, &c->dlog[0], d.log_capacity) ||
@@ -522,11 +526,13 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
     if (ordered_exec_occupancy(&occ_o) != 0 || occ_o < 1) occ_o = 1;
     c->ord_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ_o;
     c->stream_blocks = c->n_sm * 8;
+    if (validate_setup() != cudaSuccess) return fail(HETM_ECUDA);
 
     if (cudaMemsetAsync(c->locks, 0, (1ull << d.lock_log2) * 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->scr, 0, sizeof(Scratch), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->d_prefix0, 0, 16, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->TS, 0, stmr_words * 4, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->W, 0, stmr_words * 4, c->stream) != cudaSuccess ||
@@ -551,6 +557,7 @@ int hetm_load(hetm_ctx *c, const int32_t *src, uint64_t n) {
     CK(cudaMemcpyAsync(c->S, c->W, n * 4, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemsetAsync(c->TS, 0, n * 4, c->stream));
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
+    CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
     CK(cudaMemsetAsync(c->locks, 0, (1ull << c->cfg.lock_log2) * 8, c->stream));
     CK(cudaMemsetAsync(c->scr, 0, sizeof(Scratch), c->stream));
@@ -660,7 +667,7 @@ int hetm_exec_counters(hetm_ctx *c, uint64_t *committed, uint64_t *gave_up, uint
 int hetm_gpu_mark(hetm_ctx *c, const uint32_t *addr, const int32_t *vals, uint64_t n) {
     if (!c || (n && !addr)) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
-    CK(launch_mark(addr, vals, n, c->W, c->n_words, c->rs, c->gshift, c->ws, c->cshift,
+    CK(launch_mark(addr, vals, n, c->W, c->n_words, c->rs, c->filter, c->gshift, c->ws, c->cshift,
                    &c->scr->err, c->n_sm * 4, c->stream));
     return HETM_OK;
 }
@@ -708,7 +715,7 @@ int hetm_validate(hetm_ctx *c, uint64_t *n_conflicts, uint32_t *dev_flag_bits) {
     CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
     CK(cudaMemsetAsync(&c->scr->conflicts, 0, sizeof(unsigned long long), c->stream));
     CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, dev_flag_bits, &c->scr->conflicts,
-                       c->TS, &c->scr->err, c->stream_blocks, c->stream));
+                       c->TS, &c->scr->err, c->filter, c->n_sm, c->stream));
     CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream));
     CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
     if (n_conflicts) {
@@ -733,7 +740,7 @@ int hetm_validate_only(hetm_ctx *c, const hetm_log_entry *dev_log, uint64_t n,
     if (n == 0) return HETM_OK;
     CK(launch_validate_direct(dev_log, n, c->rs, c->gshift, c->n_words, dev_flag_bits,
                               reinterpret_cast<unsigned long long *>(dev_count), &c->scr->err,
-                              c->stream_blocks, c->stream));
+                              c->filter, c->n_sm, c->stream));
     return HETM_OK;
 }
 
@@ -744,6 +751,7 @@ int hetm_merge(hetm_ctx *c, int conflict) {
     CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, conflict,
                     &c->scr->dirty, c->stream_blocks, c->stream));
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
+    CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
     return HETM_OK;
 }

@@ -47,6 +47,7 @@ struct ExecArgs {
     uint32_t lock_shift;
     unsigned long long *gv;        // global commit-version clock
     uint32_t *rs;                  // RS_bmp
+    uint32_t *filter;              // its shared-memory filter (may be null)
     uint32_t gshift;               // granule(a) = a >> gshift
     uint32_t *ws;                  // WS_bmp
     uint32_t cshift;               // chunk(a) = a >> cshift
@@ -163,19 +164,47 @@ int exec_occupancy(int threads, int *blocks_per_sm);
 cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks, cudaStream_t s);
 int ordered_exec_occupancy(int *blocks_per_sm);
 
+// validation kernels: one CTA of kValThreads per SM, RS_bmp filter in shared memory
+constexpr uint32_t kFilterBits = 1u << 20;  // 128 KiB
+constexpr int kValThreads = 1024;
+
+// Filter of RS_bmp (a one-hash Bloom filter of the set granules), kept next
+// to RS_bmp: every site that sets a granule bit also sets the granule's
+// filter bit, and both are cleared together after the merge.
+__device__ __forceinline__ uint32_t filter_slot(uint32_t g) {
+    uint32_t h = g * 0x9E3779B1u;
+    h ^= h >> 15;
+    h *= 0x85EBCA77u;
+    h ^= h >> 13;
+    return __umulhi(h, kFilterBits);
+}
+
+// Set granule g in RS_bmp (and its filter bit), skipping bits already set.
+__device__ __forceinline__ void rs_mark(uint32_t *rs, uint32_t *filter, uint64_t g) {
+    const uint32_t m = 1u << (g & 31);
+    if (rs[g >> 5] & m) return;
+    atomicOr(rs + (g >> 5), m);
+    if (filter) {
+        const uint32_t sl = filter_slot((uint32_t)g);
+        atomicOr(filter + (sl >> 5), 1u << (sl & 31));
+    }
+}
+cudaError_t validate_setup();
 cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
                             uint64_t n_words, uint32_t *flags, unsigned long long *count,
-                            uint32_t *ts, int *err, int blocks, cudaStream_t s);
+                            uint32_t *ts, int *err, const uint32_t *filter, int blocks,
+                            cudaStream_t s);
 cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const uint32_t *rs,
                                    uint32_t gshift, uint64_t n_words, uint32_t *flags,
-                                   unsigned long long *count, int *err, int blocks, cudaStream_t s);
+                                   unsigned long long *count, int *err, const uint32_t *filter,
+                                   int blocks, cudaStream_t s);
 cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int32_t *S,
                          uint64_t n_words, int blocks, cudaStream_t s);
 cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_t *S,
                          uint64_t n_words, const unsigned long long *conflicts, int force,
                          unsigned long long *dirty_count, int blocks, cudaStream_t s);
 cudaError_t launch_mark(const uint32_t *addr, const int32_t *vals, uint64_t n, int32_t *W,
-                        uint64_t n_words, uint32_t *rs, uint32_t gshift, uint32_t *ws,
-                        uint32_t cshift, int *err, int blocks, cudaStream_t s);
+                        uint64_t n_words, uint32_t *rs, uint32_t *filter, uint32_t gshift,
+                        uint32_t *ws, uint32_t cshift, int *err, int blocks, cudaStream_t s);
 
 }  // namespace hetm

@@ -41,7 +41,7 @@ struct Exec {
     __device__ __forceinline__ unsigned long long *lock(uint32_t s) const { return a.locks + s; }
     __device__ __forceinline__ void mark_read(uint64_t w0, uint32_t len) const {
         for (uint64_t g = w0 >> a.gshift; g <= (w0 + len - 1) >> a.gshift; ++g)
-            atomicOr(a.rs + (g >> 5), 1u << (g & 31));
+            rs_mark(a.rs, a.filter, g);
     }
     __device__ __forceinline__ void mark_write(uint64_t w0, uint32_t len) const {
         mark_read(w0, len);

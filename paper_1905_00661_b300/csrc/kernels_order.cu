@@ -504,11 +504,7 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) s += a.W[ad[k]];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            // hot words are read by many transactions: skip bits already set
-            const uint32_t g = ad[k] >> a.gshift, m = 1u << (g & 31);
-            if (!(a.rs[g >> 5] & m)) atomicOr(a.rs + (g >> 5), m);
-        }
+        for (int k = 0; k < 4; ++k) rs_mark(a.rs, a.filter, ad[k] >> a.gshift);
         if (d.order) d.order[li] = key;
         if (d.out) static_cast<int32_t *>(d.out)[li] = s;
         if (d.status) d.status[li] = kCommitted;
@@ -521,7 +517,7 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
 
 __device__ __forceinline__ void mark_range(const ExecArgs &a, uint64_t w0, uint32_t len, bool write) {
     for (uint64_t g = w0 >> a.gshift; g <= (w0 + len - 1) >> a.gshift; ++g)
-        atomicOr(a.rs + (g >> 5), 1u << (g & 31));
+        rs_mark(a.rs, a.filter, g);
     if (write)
         for (uint64_t c = w0 >> a.cshift; c <= (w0 + len - 1) >> a.cshift; ++c)
             atomicOr(a.ws + (c >> 5), 1u << (c & 31));

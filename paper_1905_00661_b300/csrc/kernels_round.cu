@@ -10,8 +10,11 @@
 namespace hetm {
 namespace {
 
-// A warp tile is 128 log tuples = 1536 B: lane l owns tuples 4l..4l+3, read
-// as three 16-byte vectors.  Tuple j of the lane sits in these vector words:
+// A warp tile is 128 log tuples = 1536 B, loaded by three coalesced 512-byte
+// vector instructions (lane l takes vectors l, 32 + l, 64 + l), so each
+// sector of the log crosses L2 once.  The warp then swaps the tile through
+// shared memory so that lane l owns tuples 4l..4l+3, three 16-byte vectors,
+// in which tuple j of the lane sits at:
 //   addr  q0.x q0.w q1.z q2.y
 //   value q0.y q1.x q1.w q2.z
 //   ts    q0.z q1.y q2.x q2.w
@@ -19,12 +22,29 @@ struct Tile {
     uint4 q0, q1, q2;
 };
 
+constexpr int kTileVec = 96;  // 16-byte vectors per tile
+
 __device__ __forceinline__ Tile load_tile(const hetm_log_entry *log, uint64_t tile, unsigned lane) {
-    const char *p = reinterpret_cast<const char *>(log) + tile * 1536ull + lane * 48u;
+    const uint4 *p = reinterpret_cast<const uint4 *>(reinterpret_cast<const char *>(log) + tile * 1536ull);
     Tile t;
-    t.q0 = ld_stream16(p);
-    t.q1 = ld_stream16(p + 16);
-    t.q2 = ld_stream16(p + 32);
+    t.q0 = ld_stream16(p + lane);
+    t.q1 = ld_stream16(p + 32 + lane);
+    t.q2 = ld_stream16(p + 64 + lane);
+    return t;
+}
+
+// From the coalesced load order to per-lane tuple ownership (stage: this
+// warp's kTileVec vectors of shared memory).
+__device__ __forceinline__ Tile own_tile(const Tile &in, uint4 *stage, unsigned lane) {
+    stage[lane] = in.q0;
+    stage[32 + lane] = in.q1;
+    stage[64 + lane] = in.q2;
+    __syncwarp();
+    Tile t;
+    t.q0 = stage[3 * lane];
+    t.q1 = stage[3 * lane + 1];
+    t.q2 = stage[3 * lane + 2];
+    __syncwarp();
     return t;
 }
 
@@ -39,6 +59,44 @@ __device__ __forceinline__ uint32_t rs_bit(const uint32_t *rs, uint32_t a, uint3
     return (__ldg(rs + (g >> 5)) >> (g & 31)) & 1u;
 }
 
+// Shared-memory filter of RS_bmp.  Every random probe of the L2-resident
+// bitmap costs one 32-byte L2 sector, and at 16.8M probes per validation
+// those sectors, not HBM, bound the kernel.  Each CTA therefore first looks a
+// tuple's granule up in a 1M-bit hashed summary of the set granules (a Bloom
+// filter with one hash, maintained next to RS_bmp) kept in its shared
+// memory: a clear filter bit proves the granule is not in RS_bmp, and only
+// tuples whose filter bit is set probe L2.  A CTA uses the filter only while
+// at most 3/4 of its bits are set (else it would pass almost everything).
+__device__ __forceinline__ const uint32_t *load_filter(const uint32_t *filter, uint32_t *smem) {
+    __shared__ uint32_t s_fill;
+    if (threadIdx.x == 0) s_fill = 0;
+    __syncthreads();
+    if (!filter) return nullptr;
+    const uint4 *src = reinterpret_cast<const uint4 *>(filter);
+    uint4 *dst = reinterpret_cast<uint4 *>(smem);
+    uint32_t fill = 0;
+    for (uint32_t i = threadIdx.x; i < kFilterBits / 128; i += blockDim.x) {
+        const uint4 v = __ldcg(src + i);
+        dst[i] = v;
+        fill += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fill += __shfl_xor_sync(kFull, fill, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_fill, fill);
+    __syncthreads();
+    return s_fill <= kFilterBits / 4 * 3 ? smem : nullptr;
+}
+
+__device__ __forceinline__ uint32_t probe(const uint32_t *rs, const uint32_t *flt, uint32_t a,
+                                          uint32_t gshift) {
+    const uint32_t g = a >> gshift;
+    if (flt) {
+        const uint32_t sl = filter_slot(g);
+        if (!((flt[sl >> 5] >> (sl & 31)) & 1u)) return 0u;
+    }
+    return (__ldg(rs + (g >> 5)) >> (g & 31)) & 1u;
+}
+
 // Validation (Sec. IV-C): flag = RS_bmp[granule(addr)] for every tuple, the
 // flags bit-packed in log order, the hits counted.  kMax additionally raises
 // TS[addr] to the tuple's timestamp (first pass of the apply).
@@ -46,8 +104,10 @@ template <bool kMax>
 __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__ log, uint64_t n,
                                               const uint32_t *__restrict__ rs, uint32_t gshift,
                                               uint64_t n_words, uint32_t *__restrict__ flags,
-                                              unsigned long long *count, uint32_t *ts, int *err) {
+                                              unsigned long long *count, uint32_t *ts, int *err,
+                                              const uint32_t *flt, uint4 *stage) {
     const unsigned lane = threadIdx.x & 31u;
+    stage += (threadIdx.x >> 5) * kTileVec;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = (gridDim.x * (uint64_t)blockDim.x) >> 5;
     const uint64_t n_tiles = n / 128;
@@ -58,7 +118,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
     Tile next;
     if (c < n_tiles) next = load_tile(log, c, lane);
     for (; c < n_tiles; c += n_warps) {
-        Tile cur = next;
+        const Tile cur = own_tile(next, stage, lane);
         if (c + n_warps < n_tiles) next = load_tile(log, c + n_warps, lane);
         uint32_t a[4], s[4];
         int32_t v[4];
@@ -67,7 +127,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (a[j] < n_words) {
-                nib |= rs_bit(rs, a[j], gshift) << j;
+                nib |= probe(rs, flt, a[j], gshift) << j;
                 if (kMax) atomicMax(ts + a[j], s[j]);
             } else {
                 bad = true;
@@ -89,7 +149,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
             if (i < n) {
                 uint32_t a = log[i].addr;
                 if (a < n_words) {
-                    bit = rs_bit(rs, a, gshift);
+                    bit = probe(rs, flt, a, gshift);
                     if (kMax) atomicMax(ts + a, log[i].ts);
                 } else {
                     bad = true;
@@ -107,18 +167,29 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
 }
 
 template <bool kMax>
-__global__ void __launch_bounds__(256) k_validate_round(const DevRound *rp, const uint32_t *rs,
-                                                        uint32_t gshift, uint64_t n_words,
-                                                        uint32_t *flags, unsigned long long *count,
-                                                        uint32_t *ts, int *err) {
-    validate_body<kMax>(rp->log, rp->n_log, rs, gshift, n_words, flags, count, ts, err);
+__global__ void __launch_bounds__(kValThreads) k_validate_round(const DevRound *rp, const uint32_t *rs,
+                                                                uint32_t gshift, uint64_t n_words,
+                                                                uint32_t *flags,
+                                                                unsigned long long *count,
+                                                                uint32_t *ts, int *err,
+                                                                const uint32_t *filter) {
+    extern __shared__ uint4 s_dyn[];  // tile staging, then the filter
+    uint4 *stage = s_dyn;
+    const uint32_t *flt =
+        load_filter(filter, reinterpret_cast<uint32_t *>(s_dyn + kValThreads / 32 * kTileVec));
+    validate_body<kMax>(rp->log, rp->n_log, rs, gshift, n_words, flags, count, ts, err, flt, stage);
 }
 
-__global__ void __launch_bounds__(256) k_validate_direct(const hetm_log_entry *log, uint64_t n,
-                                                         const uint32_t *rs, uint32_t gshift,
-                                                         uint64_t n_words, uint32_t *flags,
-                                                         unsigned long long *count, int *err) {
-    validate_body<false>(log, n, rs, gshift, n_words, flags, count, nullptr, err);
+__global__ void __launch_bounds__(kValThreads) k_validate_direct(const hetm_log_entry *log, uint64_t n,
+                                                                 const uint32_t *rs, uint32_t gshift,
+                                                                 uint64_t n_words, uint32_t *flags,
+                                                                 unsigned long long *count, int *err,
+                                                                 const uint32_t *filter) {
+    extern __shared__ uint4 s_dyn[];  // tile staging, then the filter
+    uint4 *stage = s_dyn;
+    const uint32_t *flt =
+        load_filter(filter, reinterpret_cast<uint32_t *>(s_dyn + kValThreads / 32 * kTileVec));
+    validate_body<false>(log, n, rs, gshift, n_words, flags, count, nullptr, err, flt, stage);
 }
 
 // Apply, second pass (Sec. IV-C): after TS holds the newest timestamp of
@@ -128,9 +199,11 @@ __global__ void __launch_bounds__(256) k_validate_direct(const hetm_log_entry *l
 __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_t *__restrict__ ts,
                                                int32_t *__restrict__ W, int32_t *__restrict__ S,
                                                uint64_t n_words) {
+    __shared__ uint4 s_stage[256 / 32 * kTileVec];
     const hetm_log_entry *log = rp->log;
     const uint64_t n = rp->n_log;
     const unsigned lane = threadIdx.x & 31u;
+    uint4 *stage = s_stage + (threadIdx.x >> 5) * kTileVec;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = (gridDim.x * (uint64_t)blockDim.x) >> 5;
     const uint64_t n_tiles = n / 128;
@@ -138,7 +211,7 @@ __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_
     Tile next;
     if (c < n_tiles) next = load_tile(log, c, lane);
     for (; c < n_tiles; c += n_warps) {
-        Tile cur = next;
+        const Tile cur = own_tile(next, stage, lane);
         if (c + n_warps < n_tiles) next = load_tile(log, c + n_warps, lane);
         uint32_t a[4], s[4];
         int32_t v[4];
@@ -238,8 +311,8 @@ __global__ void __launch_bounds__(256) k_merge(const uint32_t *__restrict__ ws, 
 // recorded in RS_bmp, and writes also in WS_bmp, as a committing GPU
 // transaction would (Sec. IV-B, IV-C).
 __global__ void k_mark(const uint32_t *__restrict__ addr, const int32_t *__restrict__ vals,
-                       uint64_t n, int32_t *W, uint64_t n_words, uint32_t *rs, uint32_t gshift,
-                       uint32_t *ws, uint32_t cshift, int *err) {
+                       uint64_t n, int32_t *W, uint64_t n_words, uint32_t *rs, uint32_t *filter,
+                       uint32_t gshift, uint32_t *ws, uint32_t cshift, int *err) {
     const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         uint32_t a = addr[i];
@@ -247,8 +320,7 @@ __global__ void k_mark(const uint32_t *__restrict__ addr, const int32_t *__restr
             set_err(err, kErrAddr);
             continue;
         }
-        uint32_t g = a >> gshift;
-        atomicOr(rs + (g >> 5), 1u << (g & 31));
+        rs_mark(rs, filter, a >> gshift);
         if (vals) {
             W[a] = vals[i];
             uint32_t ch = a >> cshift;
@@ -259,20 +331,40 @@ __global__ void k_mark(const uint32_t *__restrict__ addr, const int32_t *__restr
 
 }  // namespace
 
+constexpr size_t kValSmem = kFilterBits / 8 + kValThreads / 32 * kTileVec * 16;
+
+cudaError_t validate_setup() {
+    const int smem = (int)kValSmem;
+    cudaError_t e = cudaFuncSetAttribute(k_validate_round<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_validate_round<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_validate_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
                             uint64_t n_words, uint32_t *flags, unsigned long long *count,
-                            uint32_t *ts, int *err, int blocks, cudaStream_t s) {
+                            uint32_t *ts, int *err, const uint32_t *filter, int blocks,
+                            cudaStream_t s) {
+    const size_t smem = kValSmem;
     if (ts)
-        k_validate_round<true><<<blocks, 256, 0, s>>>(rp, rs, gshift, n_words, flags, count, ts, err);
+        k_validate_round<true><<<blocks, kValThreads, smem, s>>>(rp, rs, gshift, n_words, flags, count,
+                                                                 ts, err, filter);
     else
-        k_validate_round<false><<<blocks, 256, 0, s>>>(rp, rs, gshift, n_words, flags, count, ts, err);
+        k_validate_round<false><<<blocks, kValThreads, smem, s>>>(rp, rs, gshift, n_words, flags, count,
+                                                                  ts, err, filter);
     return cudaGetLastError();
 }
 
 cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const uint32_t *rs,
                                    uint32_t gshift, uint64_t n_words, uint32_t *flags,
-                                   unsigned long long *count, int *err, int blocks, cudaStream_t s) {
-    k_validate_direct<<<blocks, 256, 0, s>>>(log, n, rs, gshift, n_words, flags, count, err);
+                                   unsigned long long *count, int *err, const uint32_t *filter,
+                                   int blocks, cudaStream_t s) {
+    const size_t smem = kValSmem;
+    k_validate_direct<<<blocks, kValThreads, smem, s>>>(log, n, rs, gshift, n_words, flags, count, err,
+                                                        filter);
     return cudaGetLastError();
 }
 
@@ -290,10 +382,10 @@ cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_
 }
 
 cudaError_t launch_mark(const uint32_t *addr, const int32_t *vals, uint64_t n, int32_t *W,
-                        uint64_t n_words, uint32_t *rs, uint32_t gshift, uint32_t *ws,
-                        uint32_t cshift, int *err, int blocks, cudaStream_t s) {
+                        uint64_t n_words, uint32_t *rs, uint32_t *filter, uint32_t gshift,
+                        uint32_t *ws, uint32_t cshift, int *err, int blocks, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_mark<<<blocks, 256, 0, s>>>(addr, vals, n, W, n_words, rs, gshift, ws, cshift, err);
+    k_mark<<<blocks, 256, 0, s>>>(addr, vals, n, W, n_words, rs, filter, gshift, ws, cshift, err);
     return cudaGetLastError();
 }
 
