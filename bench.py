@@ -34,6 +34,10 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
+# DRAM bytes (read + write) of the ordered-phase kernel per transaction of the
+# round, from one ncu capture of `bench.py --case rmw_small` (1M transactions,
+# 35.4 MB + 498.2 MB), scaled to a launch by the transaction count.
+TRAFFIC_SEG_EXEC_PER_TX = (35.4e6 + 498.2e6) / (1 << 20)
 METRIC = ("GPU committed tx/s and p99 round latency (persistent vs per-batch); "
           "validation GB/s vs HBM peak")
 LOG2W = 28
@@ -152,8 +156,7 @@ def bench_ours(args, rank, world, local_rank, inputs):
             tx = host["dev_tx"]
             with torch.cuda.stream(s):
                 tx.copy_(host["tx"][b], non_blocking=True)
-            lg = log_for_round(logs, r)
-            parts = np.array_split(lg, CPU_THREADS)
+            parts = host["logs"][r]
             th = [threading.Thread(target=ctx.cpu_log_write, args=(t, p)) for t, p in enumerate(parts)]
             [t.start() for t in th]
             [t.join() for t in th]
@@ -201,11 +204,16 @@ def bench_ours(args, rank, world, local_rank, inputs):
             "order": torch.empty(N_TX, dtype=torch.int64).pin_memory(),
             "status": torch.empty(N_TX, dtype=torch.uint8).pin_memory(),
             "out": torch.empty(N_TX, dtype=torch.int32).pin_memory()}
-    e2e_rounds = max(2, K // 2)
+    e2e_rounds = max(3, K)
+    r0 = W + K
+    # host-side CPU logs of every e2e round, prepared before timing (workload generation)
+    host["logs"] = {r: [np.ascontiguousarray(p) for p in np.array_split(log_for_round(logs, r), CPU_THREADS)]
+                    for r in range(r0, r0 + 1 + e2e_rounds)}
+    one_round(r0, host)  # warm-up: the library allocates the pinned per-thread logs once
     barrier()
     t0 = time.perf_counter()
     e2e_commit = 0
-    for r in range(W + K, W + K + e2e_rounds):
+    for r in range(r0 + 1, r0 + 1 + e2e_rounds):
         e2e_commit += one_round(r, host)["committed"]
     barrier()
     e2e_s = time.perf_counter() - t0
@@ -217,6 +225,7 @@ def bench_ours(args, rank, world, local_rank, inputs):
            "round_ms": round_ms, "e2e_s": e2e_s, "e2e_commit": e2e_commit,
            "clocks": clk.summary(), "val": val, "hbm": hbm, "peak_kind": peak_kind,
            "aborts": sum(st["aborts"] for st in stats),
+           "kernels": sum(st["n_kernels"] for st in stats),
            "gave_up": sum(st["gave_up"] for st in stats),
            "conflict_rounds": sum(st["conflict"] for st in stats),
            "ms_validate": float(np.mean([st["ms_validate"] for st in stats])),
@@ -254,6 +263,67 @@ def bench_validation(torch, h, reps=20):
     t = float(np.mean(times))
     return {"ms": t, "gbs": bytes_ / (t * 1e-3) / 1e9, "bytes": bytes_, "hits": hits,
             "hits_expected": v.n_hits_planted}
+
+
+def critical_path(tx):
+    """Longest chain of conflicting update transactions in launch order (host, from the inputs)."""
+    last, best = {}, 0
+    for row in tx[tx["flags"] == 1]["addr"].tolist():
+        lv = 1 + max(last.get(a, 0) for a in row)
+        for a in row:
+            last[a] = lv
+        best = max(best, lv)
+    return best
+
+
+def bench_w1_uniform(torch, h, init, update_frac, reps=3):
+    """The paper's W1 (Sec. V-A): 4 uniform words per transaction on the 2^28-word STMR."""
+    tx = wl.rmw_batch(seed=SEED, batch=7, n_tx=N_TX, log2_words=LOG2W, uniform=True,
+                      update_frac=update_frac)
+    with h.Context(1 << LOG2W, GRANULE, {"cpu_threads": 1}) as ctx:
+        ctx.load(init)
+        dtx = torch.from_numpy(tx.view(np.uint8)).cuda()
+        o = torch.empty(N_TX, dtype=torch.int64, device="cuda")
+        st_ = torch.empty(N_TX, dtype=torch.uint8, device="cuda")
+        out = torch.empty(N_TX, dtype=torch.int32, device="cuda")
+        ms = []
+        for r in range(reps + 1):
+            ctx.submit_batch(h.HETM_WL_RMW, dtx, o, st_, out, txid_base=r * N_TX, n_tx=N_TX)
+            st = ctx.round(stats=True)
+            if r:
+                ms.append(st["ms_exec"])
+    e = float(np.median(ms))
+    upd = int(tx["flags"].sum())
+    return {"update_frac": update_frac, "exec_ms": e, "tx_per_s": N_TX / (e * 1e-3),
+            "exec_gbs": (16 * N_TX + 16 * upd) / (e * 1e-3) / 1e9}
+
+
+def bench_cache(torch, h, n_batches=24, seed=6):
+    """Object cache: 2^22 sets x 8 ways, prefill 2^25 keys, 90% GET Zipf(0.99) over 2^26 keys;
+    uneven batches of 1K-512K requests (log-uniform) fused into one persistent launch."""
+    lay = wl.CacheLayout(SERVE_SETS_LOG2)
+    init = wl.cache_prefill(lay, 1 << 25)
+    sizes = wl.log_uniform_sizes(seed, wl.S.SIZE, n_batches, 1 << 10, 1 << 19)
+    reqs = [wl.cache_batch(seed, i, int(n), 1 << 26) for i, n in enumerate(sizes)]
+    cfg = {"cache_log2_sets": SERVE_SETS_LOG2, "cache_key_base": lay.key_base,
+           "cache_val_base": lay.val_base, "cache_lru_base": lay.gpu_lru_base,
+           "cache_ver_base": lay.ver_base, "lock_shift": 4, "cpu_threads": 1}
+    n = int(sizes.sum())
+    with h.Context(lay.n_words, GRANULE, cfg) as ctx:
+        ctx.load(init)
+        dev = [torch.from_numpy(r.view(np.uint8)).cuda() for r in reqs]
+        outs = [(torch.empty(len(r), dtype=torch.int64, device="cuda"),
+                 torch.empty(len(r), dtype=torch.uint8, device="cuda"),
+                 torch.empty(len(r), dtype=torch.int64, device="cuda")) for r in reqs]
+        ms = []
+        for rep in range(3):
+            for d, r, (o, st_, out) in zip(dev, reqs, outs):
+                ctx.submit_batch(h.HETM_WL_CACHE, d, o, st_, out, n_tx=len(r))
+            st = ctx.round(stats=True)
+            ms.append(st["ms_exec"])
+    e = float(np.median(ms[1:]))
+    return {"batches": n_batches, "requests": n, "exec_ms": e, "tx_per_s": n / (e * 1e-3),
+            "workload": "cache_2^22sets_8way_zipf0.99_2^26keys_90get_1K-512K_fused"}
 
 
 # ---------------------------------------------------------------------------
@@ -448,6 +518,9 @@ def main():
     if rank != 0:
         return
     import paper_1905_00661_b300 as h
+    chain = [critical_path(b) for b in inputs[1]]
+    w1 = [bench_w1_uniform(torch, h, inputs[0], f) for f in (0.1, 1.0)]
+    cache = bench_cache(torch, h)
     sv_in = serving_inputs(args.serve_batches)
     rates = [SERVE_RATE, 5 * SERVE_RATE, 25 * SERVE_RATE]
     serving = {"fused": [bench_serving(torch, h, sv_in, False, r) for r in rates],
@@ -472,10 +545,16 @@ def main():
                      "merge": res["ms_merge"]},
         "aborts": res["aborts"], "gave_up": res["gave_up"],
         "conflict_rounds": res["conflict_rounds"],
-        "roofline": {"kernel": "k_exec", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": "k_seg_exec (ordered executor)", "bound": "hbm", "achieved": achieved,
                      "peak": res["hbm"], "unit": "GB/s", "frac": achieved / res["hbm"],
-                     "peak_kind": res["peak_kind"], "traffic": None,
-                     "bytes_per_launch": exec_bytes},
+                     "peak_kind": res["peak_kind"],
+                     "traffic": TRAFFIC_SEG_EXEC_PER_TX * N_TX,
+                     "bytes_per_launch": exec_bytes,
+                     "note": "latency-bound by the dependency chain, see chain"},
+        "chain": {"critical_path_steps": max(chain), "per_batch": chain,
+                  "ns_per_step": exec_ms * 1e6 / float(np.mean(chain))},
+        "w1_uniform": w1,
+        "cache": cache,
         "validation": {"kernel": "k_validate_direct", "ms": val["ms"], "gbs": val["gbs"],
                        "frac": val["gbs"] / res["hbm"], "bytes": val["bytes"],
                        "hits": val["hits"], "hits_expected": val["hits_expected"],
@@ -484,7 +563,7 @@ def main():
                 "h2d_bytes_per_step": N_TX * 20 + N_LOG * 12,
                 "d2h_bytes_per_step": N_TX * (8 + 1 + 4)},
         "serving": serving,
-        "gpu_launches": 4 * K,
+        "gpu_launches": res["kernels"],
         "clocks": res["clocks"],
         "cpu_baseline": {"value": cpu["value"], "unit": "tx/s", "cores": 1, "kind": "oracle",
                          "sample": cpu["sample"]},

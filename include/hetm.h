@@ -299,6 +299,8 @@ typedef struct hetm_round_stats {
     uint64_t dirty_chunks;   /* WS_bmp chunks merged                      */
     uint32_t n_batches;      /* batches executed this round               */
     float ms_exec, ms_validate, ms_apply, ms_merge, ms_total;
+    uint32_t n_kernels;      /* kernel launches this round (graph kernel nodes) */
+    uint32_t reserved;
 } hetm_round_stats;
 
 /* One whole round: run the queued batches (persistent executor), ship the

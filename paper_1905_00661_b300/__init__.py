@@ -55,7 +55,7 @@ class hetm_round_stats(ctypes.Structure):
                 ("committed", _u64), ("gave_up", _u64), ("aborts", _u64), ("dirty_chunks", _u64),
                 ("n_batches", _u32), ("ms_exec", ctypes.c_float), ("ms_validate", ctypes.c_float),
                 ("ms_apply", ctypes.c_float), ("ms_merge", ctypes.c_float),
-                ("ms_total", ctypes.c_float)]
+                ("ms_total", ctypes.c_float), ("n_kernels", _u32), ("reserved", _u32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -108,6 +108,7 @@ struct hetm_ctx {
 
     // graphs
     cudaGraphExec_t g_exec = nullptr, g_sync = nullptr;
+    uint32_t n_kern[2] = {0, 0};  // kernel nodes of g_exec / g_sync
     cudaEvent_t ev[7] = {};  // round timing: 0/6 around the executor, 1..4 in the sync graph, 5 end
 
     OrderArgs ord{};               // ordered-executor scratch (exec_mode ORDERED)
@@ -345,7 +346,23 @@ int capture(hetm_ctx *c, cudaGraphExec_t *out, int which) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
-    CK(e);
+    if (e == cudaSuccess) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(g, nodes.data(), &nn);
+        uint32_t k = 0;
+        for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[i], &t);
+            k += t == cudaGraphNodeTypeKernel;
+        }
+        c->n_kern[which] = k;
+    }
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        CK(e);
+    }
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     CK(e);
@@ -816,6 +833,7 @@ int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     std::memcpy(c->prev_counters, c->out->counters, sizeof(c->prev_counters));
     stats->dirty_chunks = c->out->dirty;
     stats->n_batches = nb;
+    stats->n_kernels = (nb ? c->n_kern[0] : 0) + c->n_kern[1];
     float ms = 0;
     if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[6]) == cudaSuccess) stats->ms_exec = ms;
     if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) stats->ms_validate = ms;

@@ -41,6 +41,7 @@ def test_record_layouts_match_workloads():
     assert h.LOG_DTYPE == wl.LOG_DTYPE
     assert ctypes.sizeof(h.hetm_batch) == 48
     assert ctypes.sizeof(h.hetm_config) == 128
+    assert ctypes.sizeof(h.hetm_round_stats) == 88
 
 
 def test_init_rejects_bad_arguments_before_touching_the_device():

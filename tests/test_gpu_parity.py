@@ -246,6 +246,9 @@ def test_rounds_chain_with_graph(hetm, torch, mode):
                 ctx.cpu_log_write(t, lg)
             st = ctx.round(stats=True)
             assert st["rc"] == h.HETM_OK and st["n_log"] == 4000 and st["n_batches"] == 1
+            # executor (ordered: sort + turn kernels + CTA segments; optimistic: one
+            # launch) plus validation, apply and merge
+            assert st["n_kernels"] >= (9 if mode == 0 else 4)
             keys, stat, out = bo.host()
             assert (stat == 1).all() and st["committed"] == 20000
             replayed = state.copy()
