@@ -38,6 +38,10 @@ import workloads as wl  # noqa: E402
 # round, from one ncu capture of `bench.py --case rmw_small` (1M transactions,
 # 35.4 MB + 498.2 MB), scaled to a launch by the transaction count.
 TRAFFIC_SEG_EXEC_PER_TX = (35.4e6 + 498.2e6) / (1 << 20)
+# autotuner search space of the main step (both executors, three CTA sizes,
+# the granules of Sec. V-A's study and three merge chunks)
+TUNE_SPACE = {"modes": 3, "threads": [128, 256, 512], "blocks_per_sm": [0],
+              "granules": [64, 4, 1024], "ws_chunk_bytes": [4096, 16384, 65536], "reps": 2}
 METRIC = ("GPU committed tx/s and p99 round latency (persistent vs per-batch); "
           "validation GB/s vs HBM peak")
 LOG2W = 28
@@ -108,9 +112,14 @@ class Clocks:
 # the workload (shared by both arms)
 # ---------------------------------------------------------------------------
 def make_inputs(n_pool=2):
+    """GPU batches Zipf(0.99) over the lower half of the STMR, CPU logs Zipf(0.99)
+    over the upper half: the two devices' partitions of Sec. V-A, so rounds
+    validate clean and the GPU's commits survive."""
     init = wl.init_stmr(SEED, 1 << LOG2W)
-    batches = [wl.rmw_batch(seed=SEED, batch=b, n_tx=N_TX, log2_words=LOG2W) for b in range(n_pool)]
-    logs = [np.concatenate(wl.cpu_write_log(SEED, r, N_LOG, LOG2W, cpu_threads=CPU_THREADS))
+    batches = [wl.rmw_batch(seed=SEED, batch=b, n_tx=N_TX, log2_words=LOG2W - 1)
+               for b in range(n_pool)]
+    logs = [np.concatenate(wl.cpu_write_log(SEED, r, N_LOG, LOG2W - 1, cpu_threads=CPU_THREADS,
+                                            offset=1 << (LOG2W - 1)))
             for r in range(n_pool)]
     return init, batches, logs
 
@@ -133,16 +142,22 @@ def bench_ours(args, rank, world, local_rank, inputs):
     hbm, peak_kind = peaks()
     init, batches, logs = inputs
     K, W = args.steps, args.warmup
-    ctx = h.Context(1 << LOG2W, GRANULE, {"cpu_threads": CPU_THREADS, "log_capacity": N_LOG * 2,
-                                          "cpu_log_capacity": N_LOG})
-    ctx.load(init)
-    s = ctx.stream
+    base = {"cpu_threads": CPU_THREADS, "log_capacity": N_LOG * 2, "cpu_log_capacity": N_LOG}
     dev_tx = [torch.from_numpy(b.view(np.uint8)).cuda() for b in batches]
     outs = [(torch.empty(N_TX, dtype=torch.int64, device="cuda"),
              torch.empty(N_TX, dtype=torch.uint8, device="cuda"),
              torch.empty(N_TX, dtype=torch.int32, device="cuda")) for _ in batches]
     dev_logs = [torch.from_numpy(log_for_round(logs, r).view(np.uint8)).cuda()
                 for r in range(W + K)]
+    # executor shape, granule and merge chunk tuned on the first batch and log
+    t_tune = time.perf_counter()
+    tuned = h.autotune(1 << LOG2W, init, [(h.HETM_WL_RMW,) + (dev_tx[0],) + outs[0]],
+                       log=dev_logs[0], base=base, space=TUNE_SPACE)
+    t_tune = time.perf_counter() - t_tune
+    granule = tuned["granule_bytes"]
+    ctx = h.Context(1 << LOG2W, granule, dict(base, **tuned["config"]))
+    ctx.load(init)
+    s = ctx.stream
     n_upd = [int(b["flags"].sum()) for b in batches]
     torch.cuda.synchronize()
 
@@ -192,7 +207,9 @@ def bench_ours(args, rank, world, local_rank, inputs):
         ev1.record(s)
         barrier()
     ms = ev0.elapsed_time(ev1)
-    committed = sum(st["committed"] for st in stats)
+    # a round that conflicts rolls the GPU batch back (GPU-loses): only the
+    # commits of rounds that validated clean count
+    committed = sum(st["committed"] for st in stats if not st["conflict"])
     # algorithmic bytes of the executor: every committed tx reads 4 words; updates also write 4
     exec_ms = [st["ms_exec"] for st in stats]
     exec_bytes = [16 * st["committed"] + 16 * st["n_upd"] for st in stats]
@@ -214,7 +231,8 @@ def bench_ours(args, rank, world, local_rank, inputs):
     t0 = time.perf_counter()
     e2e_commit = 0
     for r in range(r0 + 1, r0 + 1 + e2e_rounds):
-        e2e_commit += one_round(r, host)["committed"]
+        st = one_round(r, host)
+        e2e_commit += 0 if st["conflict"] else st["committed"]
     barrier()
     e2e_s = time.perf_counter() - t0
 
@@ -222,6 +240,8 @@ def bench_ours(args, rank, world, local_rank, inputs):
     ctx.close()
     val = bench_validation(torch, h)
     res = {"ms": ms, "committed": committed, "exec_ms": exec_ms, "exec_bytes": exec_bytes,
+           "tuned": {"seconds": t_tune, "config": tuned["config"], "granule_bytes": granule,
+                     "candidates": len(tuned["trials"]), "trials": tuned["trials"]},
            "round_ms": round_ms, "e2e_s": e2e_s, "e2e_commit": e2e_commit,
            "clocks": clk.summary(), "val": val, "hbm": hbm, "peak_kind": peak_kind,
            "aborts": sum(st["aborts"] for st in stats),
@@ -390,7 +410,7 @@ def bench_serving(torch, h, inputs, per_batch, rate=SERVE_RATE):
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (CPU baseline / reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(inputs, frac_tx=1 / 4):
+def oracle_sample(inputs, frac_tx=1 / 4, granule=GRANULE, chunk=16384):
     """One round of the oracle on a bounded sample: the first frac of the batch
     (serial replay in input order) and the same fraction of the CPU log."""
     import oracle
@@ -403,8 +423,8 @@ def oracle_sample(inputs, frac_tx=1 / 4):
     status = np.ones(n_tx, np.uint8)
     t0 = time.perf_counter()
     replayed = init.copy()
-    out, R, D = oracle.replay_rmw(replayed, tx, order, status, GRANULE, 16384)
-    res = oracle.round_from_replay(init, replayed, R, lg, GRANULE, np.zeros(init.size, np.uint32))
+    out, R, D = oracle.replay_rmw(replayed, tx, order, status, granule, chunk)
+    res = oracle.round_from_replay(init, replayed, R, lg, granule, np.zeros(init.size, np.uint32))
     dt = time.perf_counter() - t0
     return {"value": n_tx / dt, "seconds": dt, "n_tx": n_tx, "n_log": n_log,
             "conflict": bool(res.conflict),
@@ -412,11 +432,16 @@ def oracle_sample(inputs, frac_tx=1 / 4):
                       f"{n_log} of the {N_LOG} log tuples, full 2^{LOG2W}-word STMR"}
 
 
-def config_dict(world):
+def config_dict(world, tuned=None):
+    g = tuned["granule_bytes"] if tuned else GRANULE
+    chunk = tuned["config"]["ws_chunk_bytes"] if tuned else 16384
     return {"workload": "rmw_round_zipf0.99_2^28w_4Mtx_1Mlog",
-            "stmr_words": 1 << LOG2W, "granule_bytes": GRANULE, "batch_tx": N_TX,
+            "stmr_words": 1 << LOG2W, "granule_bytes": g, "batch_tx": N_TX,
             "update_frac": 0.1, "zipf": 0.99, "cpu_log_per_round": N_LOG,
-            "cpu_threads": CPU_THREADS, "ws_chunk_bytes": 16384,
+            "partition": "GPU batch over words [0, 2^27), CPU log over [2^27, 2^28)",
+            "cpu_threads": CPU_THREADS, "ws_chunk_bytes": chunk,
+            "executor": ({k: tuned["config"][k] for k in ("exec_mode", "exec_threads", "exec_blocks")}
+                         if tuned else None),
             "l2": "inputs larger than L2 (1 GiB STMR working copy)",
             "parallelism": f"replicas{world}" if world > 1 else "single"}
 
@@ -528,7 +553,8 @@ def main():
                "workload": f"serving_poisson_bank2^{SERVE_BANK_LOG2}_cache2^{SERVE_SETS_LOG2}sets_1K-1M",
                "rates_per_s": rates, "batches": args.serve_batches}
     del sv_in
-    cpu = oracle_sample(inputs, 1 / 4)
+    tuned = res["tuned"]
+    cpu = oracle_sample(inputs, 1 / 4, tuned["granule_bytes"], tuned["config"]["ws_chunk_bytes"])
     K = args.steps
     exec_ms = float(np.mean(res["exec_ms"]))
     exec_bytes = float(np.mean(res["exec_bytes"]))
@@ -538,7 +564,13 @@ def main():
         "metric": METRIC, "value": committed / (ms * 1e-3), "unit": "tx/s",
         "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
-        "data": "synthetic", "config": config_dict(world),
+        "data": "synthetic", "config": config_dict(world, tuned),
+        "autotune": dict({k: tuned[k] for k in ("seconds", "config", "granule_bytes", "candidates")},
+                         curve=[[t["stage"], t["exec_mode"], t["exec_threads"], t["granule_bytes"],
+                                 t["ws_chunk_bytes"], round(t["ms_exec"], 3), round(t["ms_round"], 3),
+                                 t["conflicts"]] for t in tuned["trials"]],
+                         curve_fields=["stage", "exec_mode", "exec_threads", "granule_bytes",
+                                       "ws_chunk_bytes", "ms_exec", "ms_round", "conflicts"]),
         "p50_round_ms": float(np.percentile(res["round_ms"], 50)),
         "p99_round_ms": float(np.percentile(res["round_ms"], 99)),
         "phase_ms": {"exec": exec_ms, "validate": res["ms_validate"], "apply": res["ms_apply"],

@@ -122,7 +122,9 @@ typedef struct hetm_config {
     uint32_t lock_log2;        /* 2^lock_log2 striped version locks; 22   */
     uint32_t lock_shift;       /* words per lock stripe = 2^lock_shift; 0  */
     uint32_t exec_blocks;      /* executor grid; 0 = one wave (SMs x occ.) */
-    uint32_t exec_threads;     /* executor block size (multiple of 32); 256 */
+    uint32_t exec_threads;     /* executor CTA size; 256.  Ordered mode: 128,
+                                  256 or 512 transactions per CTA segment;
+                                  optimistic: multiple of 32, <= 256          */
     uint32_t max_attempts;     /* per-transaction attempt bound; 1<<20     */
     uint32_t cpu_threads;      /* number of per-thread CPU logs; 8         */
     uint32_t log_chunk_bytes;  /* H2D shipping chunk, multiple of 12; 49152 */
@@ -359,6 +361,78 @@ HETM_API int hetm_server_wait(hetm_server *s, uint64_t id, double *latency_ms);
 HETM_API int hetm_server_get_stats(hetm_server *s, hetm_server_stats *out);
 /* Drain the queue, stop the loop thread, free the server. */
 HETM_API void hetm_server_destroy(hetm_server *s);
+
+/* ------------------------------------------------------------ autotuner */
+/* The paper runs one executor shape and studies the conflict granule (Sec.
+ * V-A: 4 B against 1 KB granules, instrumentation cost against false
+ * conflicts) and the merge chunk (Sec. IV-D: 16 KB) by hand.  The autotuner
+ * measures these choices on the caller's own sample instead: it creates a
+ * scratch context per candidate on the current device (3 x stmr_words x 4
+ * bytes plus the executor's per-round state, freed after the candidate),
+ * loads `init`, and times 1 + reps whole rounds (hetm_round) of the sample
+ * batches (+ the CPU log), the first round untimed.
+ *
+ * Search, a coordinate search in three stages:
+ *   0  executor shape -- every (mode, exec_threads, blocks per SM, lock_log2)
+ *      of the space at granules[0], no CPU log; score = transactions
+ *      committed per second of execution phase;
+ *   1  granule -- each granule with the CPU log and the best shape; score =
+ *      commits of rounds that validated clean per second of round (a
+ *      conflicting round rolls the GPU batch back), or minus the round time
+ *      when every candidate conflicts;
+ *   2  merge chunk -- each ws_chunk_bytes, scored as stage 1.
+ * In stage 0 a candidate whose warm-up round is slower than cut x the best
+ * candidate so far keeps that measurement alone. */
+typedef struct hetm_tune_space {
+    uint32_t modes;             /* bit 0: HETM_EXEC_ORDERED, bit 1: OPTIMISTIC; 3 */
+    uint32_t threads[4];        /* exec_threads candidates, 0-terminated (ordered:
+                                   128/256/512; optimistic: multiple of 32 <= 256;
+                                   others are skipped per mode); 128, 256, 512  */
+    uint32_t blocks_per_sm[4];  /* grid = SMs x this; 0 = occupancy limit.  The
+                                   first entry is always tried, the rest up to
+                                   the first 0; 0, 1                           */
+    uint32_t lock_log2[4];      /* optimistic lock-table sizes, 0-terminated; 22 */
+    uint32_t granules[8];       /* conflict granules (bytes), 0-terminated;
+                                   4, 64, 1024                                  */
+    uint32_t ws_chunk_bytes[6]; /* merge chunks, 0-terminated; 1K, 4K, 16K      */
+    uint32_t reps;              /* timed rounds per candidate (median); 3       */
+    float cut;                  /* stage-0 early cut factor; 4                  */
+} hetm_tune_space;
+
+/* One measured candidate. */
+typedef struct hetm_tune_trial {
+    uint32_t stage;             /* 0 shape, 1 granule, 2 merge chunk            */
+    uint32_t exec_mode, exec_threads, exec_blocks, lock_log2;
+    uint32_t granule_bytes, ws_chunk_bytes;
+    int32_t rc;                 /* HETM_OK, or why the candidate failed          */
+    uint32_t rounds;            /* rounds measured                               */
+    uint32_t conflicts;         /* of those, rounds that conflicted              */
+    uint64_t committed;         /* GPU commits per round (median round)          */
+    float ms_exec, ms_round;    /* medians over the measured rounds              */
+    float score;                /* the stage's score (higher is better)          */
+    uint32_t reserved;
+} hetm_tune_trial;
+
+HETM_API int hetm_tune_space_default(hetm_tune_space *space);
+
+/* Tune for a sample.  init: stmr_words int32 (host or device).  batches:
+ * n_batches descriptors as for hetm_gpu_submit_batch (device records; the
+ * output buffers are overwritten by every candidate).  log: n_log device
+ * log entries attached to every round of stages 1-2 (NULL/0: none; 16-byte
+ * aligned).  base: every field the search does not set (capacities, cache
+ * layout, allocator); NULL = defaults.  space NULL = defaults.  On
+ * HETM_OK, *best_cfg = base with exec_mode, exec_threads, exec_blocks,
+ * lock_log2 and ws_chunk_bytes tuned and *best_granule is the granule to
+ * pass to hetm_init.  trials (may be NULL when max_trials is 0) receives up
+ * to max_trials candidates in the order run; *n_trials (may be NULL) the
+ * number run.  Synchronous; do not run it while another context of the
+ * same device is mid-round if timings are to mean anything.
+ * HETM_EINVAL for bad arguments or when no stage-0 candidate ran. */
+HETM_API int hetm_autotune(uint64_t stmr_words, const int32_t *init, const hetm_batch *batches,
+                           uint32_t n_batches, const hetm_log_entry *log, uint64_t n_log,
+                           const hetm_config *base, const hetm_tune_space *space,
+                           hetm_config *best_cfg, uint32_t *best_granule, hetm_tune_trial *trials,
+                           uint32_t max_trials, uint32_t *n_trials);
 
 #ifdef __cplusplus
 }

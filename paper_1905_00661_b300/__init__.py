@@ -69,7 +69,24 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_merge", "hetm_round", "hetm_validate_noalloc", "hetm_ctx_stream",
            "hetm_round_wait", "hetm_server_config_default", "hetm_server_create",
            "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
-           "hetm_server_destroy")
+           "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune")
+
+
+class hetm_tune_space(ctypes.Structure):
+    _fields_ = [("modes", _u32), ("threads", _u32 * 4), ("blocks_per_sm", _u32 * 4),
+                ("lock_log2", _u32 * 4), ("granules", _u32 * 8), ("ws_chunk_bytes", _u32 * 6),
+                ("reps", _u32), ("cut", ctypes.c_float)]
+
+
+class hetm_tune_trial(ctypes.Structure):
+    _fields_ = [("stage", _u32), ("exec_mode", _u32), ("exec_threads", _u32),
+                ("exec_blocks", _u32), ("lock_log2", _u32), ("granule_bytes", _u32),
+                ("ws_chunk_bytes", _u32), ("rc", _i32), ("rounds", _u32), ("conflicts", _u32),
+                ("committed", _u64), ("ms_exec", ctypes.c_float), ("ms_round", ctypes.c_float),
+                ("score", ctypes.c_float), ("reserved", _u32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 class hetm_request(ctypes.Structure):
@@ -128,6 +145,10 @@ def _declare(L):
         "hetm_server_wait": (_int, [_vp, _u64, P(ctypes.c_double)]),
         "hetm_server_get_stats": (_int, [_vp, P(hetm_server_stats)]),
         "hetm_server_destroy": (None, [_vp]),
+        "hetm_tune_space_default": (_int, [P(hetm_tune_space)]),
+        "hetm_autotune": (_int, [_u64, _vp, P(hetm_batch), _u32, _vp, _u64, P(hetm_config),
+                                 P(hetm_tune_space), P(hetm_config), P(_u32), P(hetm_tune_trial),
+                                 _u32, P(_u32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -204,6 +225,62 @@ def hetm_validate_noalloc(dev_log, n, dev_rs_bmp, granule_bytes, stmr_words, dev
     return _lib.hetm_validate_noalloc(_ptr(dev_log), n, _ptr(dev_rs_bmp), granule_bytes,
                                       stmr_words, _ptr(dev_flag_bits), _ptr(dev_n_conflicts),
                                       _ptr(dev_err), stream)
+
+
+def hetm_tune_space_default() -> hetm_tune_space:
+    sp = hetm_tune_space()
+    _ck(_lib.hetm_tune_space_default(ctypes.byref(sp)), "hetm_tune_space_default")
+    return sp
+
+
+_TUNED = ("exec_mode", "exec_threads", "exec_blocks", "lock_log2", "ws_chunk_bytes")
+
+
+def autotune(stmr_words, init, batches, log=None, n_log=None, base=None, space=None,
+             max_trials=128):
+    """Pick the executor shape, conflict granule and merge chunk for a sample
+    (hetm_autotune).  ``batches``: list of (workload, tx, order, status, out)
+    or dicts with those keys plus optional n_tx / txid_base / word_base, device
+    tensors.  ``log``: device tensor of log entries or None.  ``base`` and
+    ``space``: dicts of hetm_config / hetm_tune_space fields.  Returns
+    {"config": tuned fields, "granule_bytes": G, "trials": [...]}."""
+    import torch
+    if isinstance(init, np.ndarray):
+        init = np.ascontiguousarray(init, dtype=np.int32)
+    torch.cuda.current_stream().synchronize()
+    descs = (hetm_batch * len(batches))()
+    for i, b in enumerate(batches):
+        if not isinstance(b, dict):
+            b = dict(zip(("workload", "tx", "order", "status", "out"), b))
+        tx = b["tx"]
+        n_tx = b.get("n_tx")
+        if n_tx is None:
+            n_tx = len(tx) if isinstance(tx, np.ndarray) else tx.numel() * tx.element_size() // {
+                HETM_WL_BANK: 12, HETM_WL_RMW: 20, HETM_WL_CACHE: 24}[b["workload"]]
+        descs[i] = hetm_batch(b["workload"], int(n_tx), _ptr(tx), _ptr(b.get("order")),
+                              _ptr(b.get("status")), _ptr(b.get("out")), b.get("txid_base", 0),
+                              b.get("word_base", 0))
+    cfg = hetm_config_default()
+    for k, v in (base or {}).items():
+        setattr(cfg, k, v)
+    sp = hetm_tune_space_default()
+    for k, v in (space or {}).items():
+        if isinstance(getattr(sp, k), ctypes.Array):
+            arr = getattr(sp, k)
+            for j in range(len(arr)):
+                arr[j] = v[j] if j < len(v) else 0
+        else:
+            setattr(sp, k, v)
+    if log is not None and n_log is None:
+        n_log = log.numel() * log.element_size() // 12
+    best, g = hetm_config(), _u32()
+    trials = (hetm_tune_trial * max_trials)()
+    nt = _u32()
+    _ck(_lib.hetm_autotune(int(stmr_words), _ptr(init), descs, len(batches), _ptr(log),
+                           int(n_log or 0), ctypes.byref(cfg), ctypes.byref(sp), ctypes.byref(best),
+                           ctypes.byref(g), trials, max_trials, ctypes.byref(nt)), "hetm_autotune")
+    return {"config": {k: getattr(best, k) for k in _TUNED}, "granule_bytes": g.value,
+            "trials": [trials[i].as_dict() for i in range(min(nt.value, max_trials))]}
 
 
 # ---------------------------------------------------------------------------

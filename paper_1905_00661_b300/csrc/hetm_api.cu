@@ -448,7 +448,12 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
     if (cfg) d = *cfg;
     if (!pow2(d.ws_chunk_bytes) || d.ws_chunk_bytes < 16) return HETM_EINVAL;
     if (d.lock_log2 < 1 || d.lock_log2 > 30 || d.lock_shift > 31) return HETM_EINVAL;
-    if (d.exec_threads == 0 || d.exec_threads % 32 || d.exec_threads > 256) return HETM_EINVAL;
+    if (d.exec_mode == HETM_EXEC_ORDERED) {
+        if (d.exec_threads != 128 && d.exec_threads != 256 && d.exec_threads != 512)
+            return HETM_EINVAL;
+    } else if (d.exec_threads == 0 || d.exec_threads % 32 || d.exec_threads > 256) {
+        return HETM_EINVAL;
+    }
     if (d.log_chunk_bytes < 12 || d.log_chunk_bytes % 12 || d.max_attempts == 0) return HETM_EINVAL;
     if (d.max_batches == 0 || d.max_batches > 65535 || d.cpu_threads == 0 || d.log_capacity == 0)
         return HETM_EINVAL;
@@ -500,6 +505,7 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         OrderArgs &o = c->ord;
         o.cap_tx = (uint32_t)d.max_round_tx;
         o.cap_acc = 4 * o.cap_tx;
+        o.seg_log2 = (uint32_t)ilog2(d.exec_threads);
         o.key_bits = (uint32_t)ilog2(stmr_words);
         if (o.key_bits == 0) o.key_bits = 1;
         const uint64_t hist_n = 256ull * ((o.cap_acc + 2047) / 2048);
@@ -537,11 +543,13 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
 
     int occ = 0;
     c->exec_threads = (int)d.exec_threads;
-    if (exec_occupancy(c->exec_threads, &occ) != 0 || occ < 1) occ = 1;
-    c->exec_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ;
-    int occ_o = 0;
-    if (ordered_exec_occupancy(&occ_o) != 0 || occ_o < 1) occ_o = 1;
-    c->ord_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ_o;
+    if (d.exec_mode == HETM_EXEC_ORDERED) {
+        if (ordered_exec_occupancy(d.exec_threads, &occ) != 0 || occ < 1) occ = 1;
+        c->ord_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ;
+    } else {
+        if (exec_occupancy(c->exec_threads, &occ) != 0 || occ < 1) occ = 1;
+        c->exec_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ;
+    }
     c->stream_blocks = c->n_sm * 8;
     if (validate_setup() != cudaSuccess) return fail(HETM_ECUDA);
 

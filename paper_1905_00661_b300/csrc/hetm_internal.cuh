@@ -66,7 +66,7 @@ struct ExecArgs {
 // One transaction of the ordered phase (indexed by its rank in that phase).
 // Slot k of a word transaction is one distinct word; turn[k] carries the
 // access's position among the accesses to its resource plus flags.
-constexpr uint32_t kSeg = 256;              // transactions per CTA segment
+constexpr uint32_t kSegMin = 128, kSegMax = 512;  // CTA segment sizes (threads)
 constexpr uint32_t kTurnMask = 0x0FFFFFFFu;
 constexpr uint32_t kFWriter = 1u << 31;     // the access writes the resource
 constexpr uint32_t kFLast = 1u << 30;       // last access of the word in the launch
@@ -98,6 +98,7 @@ struct OrderArgs {
     uint32_t *n_acc, *n_ord, *n_tx32;
     unsigned long long *v0;     // commit clock before the launch
     uint32_t cap_tx, cap_acc, key_bits;
+    uint32_t seg_log2;          // transactions per CTA segment = 2^seg_log2 (7, 8 or 9)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -162,7 +163,7 @@ __device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
 cudaError_t launch_exec(const ExecArgs &a, int blocks, int threads, cudaStream_t s);
 int exec_occupancy(int threads, int *blocks_per_sm);
 cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks, cudaStream_t s);
-int ordered_exec_occupancy(int *blocks_per_sm);
+int ordered_exec_occupancy(uint32_t seg, int *blocks_per_sm);
 
 // validation kernels: one CTA of kValThreads per SM, RS_bmp filter in shared memory
 constexpr uint32_t kFilterBits = 1u << 20;  // 128 KiB

@@ -459,14 +459,14 @@ __global__ void __launch_bounds__(256) k_ord_acc(OrderArgs o) {
             turn = ((uint32_t)i - start) | kFWriter;
             if (i > start) {
                 const uint32_t pv = o.vals0[i - 1];
-                if ((pv >> 4) / kSeg == rank / kSeg) {
+                if ((pv >> 4) >> o.seg_log2 == rank >> o.seg_log2) {
                     turn |= kFLocal;
-                    src = (((pv >> 4) % kSeg) << 2) | ((pv >> 2) & 3u);
+                    src = (((pv >> 4) & ((1u << o.seg_log2) - 1u)) << 2) | ((pv >> 2) & 3u);
                 }
             }
             const bool last = i + 1 == n || o.keys0[i + 1] != o.keys0[i];
             if (last) turn |= kFLast;
-            else if ((o.vals0[i + 1] >> 4) / kSeg != rank / kSeg) turn |= kFPublish;
+            else if ((o.vals0[i + 1] >> 4) >> o.seg_log2 != rank >> o.seg_log2) turn |= kFPublish;
         }
         OrdRec &r = o.rec[rank];
         r.res[k] = start;
@@ -602,8 +602,8 @@ __device__ void cache_request(const ExecArgs &a, const hetm_cache_req &r, uint32
 
 constexpr long long kPollCycles = 1000;  // ~0.5 us: one L2 round trip
 
-// Ordered phase: CTA segments of kSeg consecutive ranks, handed out in rank
-// order.  Thread t owns rank g*kSeg + t.  Each warp runs its 32 transactions
+// Ordered phase: CTA segments of SEG consecutive ranks, handed out in rank
+// order.  Thread t owns rank g*SEG + t.  Each warp runs its 32 transactions
 // in waves: in one wave every lane whose inputs are all available executes
 // (lanes that are ready at the same time never depend on each other), then
 // the warp syncs.  Inputs come from a predecessor in the same warp (done in
@@ -612,15 +612,16 @@ constexpr long long kPollCycles = 1000;  // ~0.5 us: one L2 round trip
 // (turns done, value) word, polled once per wave, the load issued a wave
 // ahead so its latency overlaps the warp's work).  No lane ever spins while a
 // lane it waits for sits in the same warp.
-__global__ void __launch_bounds__(kSeg) k_seg_exec(OrderArgs o) {
+template <uint32_t SEG>
+__global__ void __launch_bounds__(SEG) k_seg_exec(OrderArgs o) {
     // (segment + 1) << 32 | value: one aligned 8-byte store hands a word on
     // to a later transaction of the segment, flag and data together
-    __shared__ unsigned long long s_pack[kSeg][4];
+    __shared__ unsigned long long s_pack[SEG][4];
     __shared__ uint32_t s_seg;
     __shared__ int s_abort;
     const ExecArgs &a = o.e;
     const uint32_t n_ord = *o.n_ord;
-    const uint32_t n_seg = (n_ord + kSeg - 1) / kSeg;
+    const uint32_t n_seg = (n_ord + SEG - 1) / SEG;
     const unsigned long long v0 = *o.v0;
     const unsigned t = threadIdx.x;
     const unsigned long long t0 = __shfl_sync(kFull, globaltimer_ns(), 0);
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(kSeg) k_seg_exec(OrderArgs o) {
         __syncthreads();
         const uint32_t g = s_seg;
         if (g >= n_seg) break;
-        const uint32_t r = g * kSeg + t;
+        const uint32_t r = g * SEG + t;
         OrdRec rc;
         uint32_t n = 0, wl = 0;
         if (r < n_ord) {
@@ -851,12 +852,22 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
     k_ord_ro<<<stream_blocks, 256, 0, s>>>(o);
     e = cudaMemsetAsync(o.e.next, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_seg_exec<<<exec_blocks, kSeg, 0, s>>>(o);
+    switch (o.seg_log2) {
+    case 7: k_seg_exec<128><<<exec_blocks, 128, 0, s>>>(o); break;
+    case 8: k_seg_exec<256><<<exec_blocks, 256, 0, s>>>(o); break;
+    case 9: k_seg_exec<512><<<exec_blocks, 512, 0, s>>>(o); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-int ordered_exec_occupancy(int *blocks_per_sm) {
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec, kSeg, 0);
+int ordered_exec_occupancy(uint32_t seg, int *blocks_per_sm) {
+    switch (seg) {
+    case 128: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec<128>, 128, 0);
+    case 256: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec<256>, 256, 0);
+    case 512: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec<512>, 512, 0);
+    default: return (int)cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace hetm

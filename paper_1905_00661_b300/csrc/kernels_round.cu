@@ -54,11 +54,6 @@ __device__ __forceinline__ void tile_fields(const Tile &t, uint32_t a[4], int32_
     s[0] = t.q0.z; s[1] = t.q1.y; s[2] = t.q2.x; s[3] = t.q2.w;
 }
 
-__device__ __forceinline__ uint32_t rs_bit(const uint32_t *rs, uint32_t a, uint32_t gshift) {
-    uint32_t g = a >> gshift;
-    return (__ldg(rs + (g >> 5)) >> (g & 31)) & 1u;
-}
-
 // Shared-memory filter of RS_bmp.  Every random probe of the L2-resident
 // bitmap costs one 32-byte L2 sector, and at 16.8M probes per validation
 // those sectors, not HBM, bound the kernel.  Each CTA therefore first looks a

@@ -54,3 +54,17 @@ def test_init_rejects_bad_arguments_before_touching_the_device():
     cfg = h.hetm_config_default()
     cfg.ws_chunk_bytes = 100
     assert L.hetm_init(ctypes.byref(p), 1024, 64, ctypes.byref(cfg), None) == h.HETM_EINVAL
+
+
+def test_autotune_space_and_argument_checks_without_gpu():
+    import paper_1905_00661_b300 as h
+    assert ctypes.sizeof(h.hetm_tune_space) == 116
+    assert ctypes.sizeof(h.hetm_tune_trial) == 64
+    sp = h.hetm_tune_space_default()
+    assert sp.modes == 3 and list(sp.threads) == [128, 256, 512, 0]
+    assert list(sp.granules)[:4] == [4, 64, 1024, 0] and sp.reps == 3
+    best, g = h.hetm_config(), ctypes.c_uint32()
+    # no sample: rejected before any device call
+    rc = h.lib().hetm_autotune(1 << 10, None, None, 0, None, 0, None, None, ctypes.byref(best),
+                               ctypes.byref(g), None, 0, None)
+    assert rc == h.HETM_EINVAL

@@ -422,16 +422,20 @@ def rmw_batch(seed: int, batch: int, n_tx: int, log2_words: int, q: float = 0.99
 
 def cpu_write_log(seed: int, rnd: int, n: int, log2_words: int, q: float = 0.99,
                   ts_base: int = 0, cpu_threads: int = 4, uniform: bool = False,
-                  lo: int = 0, hi: int | None = None) -> list:
-    """Per-thread CPU logs of plain writes for one round; ts = ts_base + 1 .. ts_base + n."""
+                  lo: int = 0, hi: int | None = None, offset: int = 0) -> list:
+    """Per-thread CPU logs of plain writes for one round; ts = ts_base + 1 .. ts_base + n.
+
+    Zipf addresses fall in [offset, offset + 2^log2_words): with ``offset`` the
+    log covers another partition of the STMR than the GPU's (Sec. V-A splits
+    the STMR in two halves, one per device)."""
     n_words = 1 << log2_words
     hi = n_words if hi is None else hi
     if uniform:
         addr = (uniform_below(draws_range(seed, S.LOG_ADDR, n, rnd * n), hi - lo)
                 + np.uint64(lo)).astype(np.uint32)
     else:
-        addr = rank_to_index(Zipf(n_words, q).sample(seed, S.LOG_ADDR, n, start=rnd * n),
-                             log2_words)
+        addr = (rank_to_index(Zipf(n_words, q).sample(seed, S.LOG_ADDR, n, start=rnd * n),
+                              log2_words).astype(np.uint64) + np.uint64(offset)).astype(np.uint32)
     val = (draws_range(seed, S.LOG_VAL, n, rnd * n) >> np.uint64(32)).astype(np.uint32).view(np.int32)
     log = np.zeros(n, dtype=LOG_DTYPE)
     log["addr"], log["value"] = addr, val
