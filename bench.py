@@ -236,9 +236,12 @@ def bench_ours(args, rank, world, local_rank, inputs):
     barrier()
     e2e_s = time.perf_counter() - t0
 
-    # ---- validation kernel on the validation-at-scale input
+    # ---- validation kernel, and the whole sync phase, on the validation-at-scale input
     ctx.close()
-    val = bench_validation(torch, h)
+    vround = wl.validation_round(seed=1, log2_words=LOG2W, with_init=False)
+    val = bench_validation(torch, h, vround)
+    val["round"] = bench_round_at_scale(torch, h, vround)
+    del vround
     res = {"ms": ms, "committed": committed, "exec_ms": exec_ms, "exec_bytes": exec_bytes,
            "tuned": {"seconds": t_tune, "config": tuned["config"], "granule_bytes": granule,
                      "candidates": len(tuned["trials"]), "trials": tuned["trials"]},
@@ -254,9 +257,8 @@ def bench_ours(args, rank, world, local_rank, inputs):
     return res
 
 
-def bench_validation(torch, h, reps=20):
+def bench_validation(torch, h, v, reps=20):
     """Kernel V alone on the 16M-tuple log (12 B/tuple + 1 flag bit), 2^28 words, G = 64 B."""
-    v = wl.validation_round(seed=1, log2_words=LOG2W, with_init=False)
     n = len(v.log)
     with h.Context(1 << LOG2W, v.granule_bytes, {"log_capacity": 1 << 12}) as vc:
         first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
@@ -283,6 +285,48 @@ def bench_validation(torch, h, reps=20):
     t = float(np.mean(times))
     return {"ms": t, "gbs": bytes_ / (t * 1e-3) / 1e9, "bytes": bytes_, "hits": hits,
             "hits_expected": v.n_hits_planted}
+
+
+def bench_round_at_scale(torch, h, v, reps=5):
+    """Validation + apply + merge of the validation-at-scale round (2^28 words,
+    G = 64 B, 16 KB chunks): planted read set and GPU writes, 16M-entry CPU log.
+    Two variants: the log as generated (2% hits: conflict, dirty chunks S -> W)
+    and the log without its hits (clean: dirty chunks W -> S)."""
+    wpg = v.granule_bytes // 4
+    first = torch.from_numpy((v.read_granules.astype(np.uint64) * wpg).astype(np.uint32)).cuda()
+    paddr = torch.from_numpy(v.plant_addr).cuda()
+    pval = torch.from_numpy(v.plant_value).cuda()
+    is_read = np.zeros((1 << LOG2W) // wpg, dtype=bool)
+    is_read[v.read_granules] = True
+    out = {}
+    for name, lg in (("conflict", v.log), ("clean", v.log[~is_read[v.log["addr"] // wpg]])):
+        dlog = torch.from_numpy(np.ascontiguousarray(lg).view(np.uint8)).cuda()
+        n = len(lg)
+        with h.Context(1 << LOG2W, v.granule_bytes, {"log_capacity": 1 << 12, "cpu_threads": 1}) as c:
+            c.load(torch.zeros(1 << LOG2W, dtype=torch.int32, device="cuda"))
+            rows = []
+            for r in range(reps + 1):
+                c.gpu_mark(first)
+                c.gpu_mark(paddr, pval)
+                c.log_attach(dlog, n)
+                st = c.round(stats=True)
+                if r:
+                    rows.append(st)
+        chunk = 16384
+        ms_v = float(np.median([x["ms_validate"] for x in rows]))
+        ms_a = float(np.median([x["ms_apply"] for x in rows]))
+        ms_m = float(np.median([x["ms_merge"] for x in rows]))
+        dirty = rows[-1]["dirty_chunks"]
+        # distinct winning entries: one per distinct address (newest ts)
+        n_win = int(np.unique(lg["addr"]).size)
+        out[name] = {
+            "n_log": n, "conflict": bool(rows[-1]["conflict"]), "n_conflicts": rows[-1]["n_conflicts"],
+            "validate_ts_ms": ms_v, "validate_ts_gbs": (16 * n + n / 8) / (ms_v * 1e-3) / 1e9,
+            "apply_ms": ms_a, "apply_gbs": (12 * n + 8 * n_win) / (ms_a * 1e-3) / 1e9,
+            "merge_ms": ms_m, "dirty_chunks": dirty,
+            "merge_gbs": 2 * dirty * chunk / (ms_m * 1e-3) / 1e9,
+        }
+    return out
 
 
 def critical_path(tx):
@@ -544,6 +588,7 @@ def main():
         return
     import paper_1905_00661_b300 as h
     chain = [critical_path(b) for b in inputs[1]]
+    handoff_g, handoff_s = h.handoff_latency(20000)
     w1 = [bench_w1_uniform(torch, h, inputs[0], f) for f in (0.1, 1.0)]
     cache = bench_cache(torch, h)
     sv_in = serving_inputs(args.serve_batches)
@@ -584,13 +629,19 @@ def main():
                      "bytes_per_launch": exec_bytes,
                      "note": "latency-bound by the dependency chain, see chain"},
         "chain": {"critical_path_steps": max(chain), "per_batch": chain,
-                  "ns_per_step": exec_ms * 1e6 / float(np.mean(chain))},
+                  "ns_per_step": exec_ms * 1e6 / float(np.mean(chain)),
+                  "handoff_ns": {"cross_sm_global": handoff_g, "cross_warp_shared": handoff_s},
+                  # serialization-depth bound: every step of the longest chain
+                  # costs at least one hand-on (all inside CTAs: the floor)
+                  "bound_ms": float(np.mean(chain)) * handoff_s * 1e-6,
+                  "frac_of_bound": float(np.mean(chain)) * handoff_s * 1e-6 / exec_ms},
         "w1_uniform": w1,
         "cache": cache,
         "validation": {"kernel": "k_validate_direct", "ms": val["ms"], "gbs": val["gbs"],
                        "frac": val["gbs"] / res["hbm"], "bytes": val["bytes"],
                        "hits": val["hits"], "hits_expected": val["hits_expected"],
-                       "workload": "validation_2^28w_16Mlog_g64"},
+                       "workload": "validation_2^28w_16Mlog_g64",
+                       "sync_phase": val["round"]},
         "e2e": {"value": e2e_commit / e2e_s, "unit": "tx/s",
                 "h2d_bytes_per_step": N_TX * 20 + N_LOG * 12,
                 "d2h_bytes_per_step": N_TX * (8 + 1 + 4)},

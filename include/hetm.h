@@ -362,6 +362,20 @@ HETM_API int hetm_server_get_stats(hetm_server *s, hetm_server_stats *out);
 /* Drain the queue, stop the loop thread, free the server. */
 HETM_API void hetm_server_destroy(hetm_server *s);
 
+/* ---------------------------------------------------- handoff latency */
+/* Committing in a fixed order serializes the writers of every word, so a
+ * batch cannot execute faster than its longest chain of conflicting
+ * transactions times the time one transaction needs to hand a word on to
+ * the next (the serialization-depth bound).  This measures that hand-on on
+ * the current device with nothing else running: *global_ns, a token
+ * bounced between two CTAs on two SMs through one global word (acquire
+ * load / release store, cooperative launch); *shared_ns, between two warps
+ * of one CTA through shared memory.  Each is the mean over 2 x rounds
+ * one-way hand-ons.  Either pointer may be NULL.  Synchronous; allocates 40
+ * bytes of device memory for the call.  Every wait is bounded (1 s):
+ * HETM_ETIMEOUT if one gave up. */
+HETM_API int hetm_handoff_latency(uint32_t rounds, double *global_ns, double *shared_ns);
+
 /* ------------------------------------------------------------ autotuner */
 /* The paper runs one executor shape and studies the conflict granule (Sec.
  * V-A: 4 B against 1 KB granules, instrumentation cost against false

@@ -69,7 +69,8 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_merge", "hetm_round", "hetm_validate_noalloc", "hetm_ctx_stream",
            "hetm_round_wait", "hetm_server_config_default", "hetm_server_create",
            "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
-           "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune")
+           "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune",
+           "hetm_handoff_latency")
 
 
 class hetm_tune_space(ctypes.Structure):
@@ -146,6 +147,7 @@ def _declare(L):
         "hetm_server_get_stats": (_int, [_vp, P(hetm_server_stats)]),
         "hetm_server_destroy": (None, [_vp]),
         "hetm_tune_space_default": (_int, [P(hetm_tune_space)]),
+        "hetm_handoff_latency": (_int, [_u32, P(ctypes.c_double), P(ctypes.c_double)]),
         "hetm_autotune": (_int, [_u64, _vp, P(hetm_batch), _u32, _vp, _u64, P(hetm_config),
                                  P(hetm_tune_space), P(hetm_config), P(_u32), P(hetm_tune_trial),
                                  _u32, P(_u32)]),
@@ -231,6 +233,14 @@ def hetm_tune_space_default() -> hetm_tune_space:
     sp = hetm_tune_space()
     _ck(_lib.hetm_tune_space_default(ctypes.byref(sp)), "hetm_tune_space_default")
     return sp
+
+
+def handoff_latency(rounds=20000):
+    """(cross-SM ns, cross-warp ns) for one hand-on of a word (hetm_handoff_latency)."""
+    g, sh = ctypes.c_double(), ctypes.c_double()
+    _ck(_lib.hetm_handoff_latency(int(rounds), ctypes.byref(g), ctypes.byref(sh)),
+        "hetm_handoff_latency")
+    return g.value, sh.value
 
 
 _TUNED = ("exec_mode", "exec_threads", "exec_blocks", "lock_log2", "ws_chunk_bytes")

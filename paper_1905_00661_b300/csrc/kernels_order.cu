@@ -600,41 +600,153 @@ __device__ void cache_request(const ExecArgs &a, const hetm_cache_req &r, uint32
     out = way;
 }
 
-constexpr long long kPollCycles = 1000;  // ~0.5 us: one L2 round trip
+// Ordered phase, CTA-segment executor.  A CTA takes segments of SEG
+// consecutive ranks in rank order; executor thread t owns rank g*SEG + t,
+// and one extra warp (the poll warp) watches the words that earlier segments
+// hand on.  Each executor warp runs its 32 transactions in waves: in one
+// wave every lane whose inputs are all available executes (lanes ready at
+// the same time never depend on each other), then the warp syncs.  Inputs
+// come from a predecessor in the same segment (its value in shared memory,
+// tagged with the segment) or from an earlier segment (the resource's packed
+// (turns done, value) word in global memory).  The executor warps issue no
+// global load inside the wave loop: a load in flight would stall the whole
+// warp, and with it the lanes at the front of a chain, for an L2 round trip
+// at every wave.  Instead each lane checks its external inputs once when the
+// segment starts, and the poll warp polls the ones still pending and hands
+// each one over through shared memory as soon as it is satisfied.  Idle
+// warps sleep in proportion to how far their nearest lane is from its turn
+// (the poll warp records the gap of external waits; a local wait is one more
+// than its predecessor's), so that the warps at the front of the chains get
+// the issue slots.
+#ifndef HETM_SLEEP_PER_TURN
+#define HETM_SLEEP_PER_TURN 32  // ns of sleep per turn still ahead of an idle warp
+#endif
 
-// Ordered phase: CTA segments of SEG consecutive ranks, handed out in rank
-// order.  Thread t owns rank g*SEG + t.  Each warp runs its 32 transactions
-// in waves: in one wave every lane whose inputs are all available executes
-// (lanes that are ready at the same time never depend on each other), then
-// the warp syncs.  Inputs come from a predecessor in the same warp (done in
-// an earlier wave, value in shared memory), in another warp of the segment
-// (shared-memory done flag), or in an earlier segment (the resource's packed
-// (turns done, value) word, polled once per wave, the load issued a wave
-// ahead so its latency overlaps the warp's work).  No lane ever spins while a
-// lane it waits for sits in the same warp.
 template <uint32_t SEG>
-__global__ void __launch_bounds__(SEG) k_seg_exec(OrderArgs o) {
+struct SegSmem {
     // (segment + 1) << 32 | value: one aligned 8-byte store hands a word on
     // to a later transaction of the segment, flag and data together
-    __shared__ unsigned long long s_pack[SEG][4];
-    __shared__ uint32_t s_seg;
-    __shared__ int s_abort;
+    unsigned long long pack[SEG][4];  // this lane's output for slot k
+    unsigned long long ext[SEG][4];   // external input of slot k, from the poll warp
+    uint32_t list_slot[SEG * 4];      // pending external slots: t << 2 | k
+    uint32_t list_res[SEG * 4];       //   their resource
+    uint32_t list_turn[SEG * 4];      //   their turn word
+    uint32_t gap[SEG];                // min turns still ahead over the lane's external waits
+    uint32_t eff[SEG];                // the lane's distance estimate, for its local successors
+    uint32_t seg, n_list;
+    int abort;
+};
+
+template <uint32_t SEG>
+__global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SegSmem<SEG> &sm = *reinterpret_cast<SegSmem<SEG> *>(smem_raw);
     const ExecArgs &a = o.e;
     const uint32_t n_ord = *o.n_ord;
     const uint32_t n_seg = (n_ord + SEG - 1) / SEG;
     const unsigned long long v0 = *o.v0;
     const unsigned t = threadIdx.x;
+    const unsigned lane = t & 31u;
+    const bool poller = t >= SEG;
     const unsigned long long t0 = __shfl_sync(kFull, globaltimer_ns(), 0);
     unsigned long long n_commit = 0, n_gaveup = 0;
+    if (!poller) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) s_pack[t][k] = 0ull;
-    if (t == 0) s_abort = 0;
+        for (int k = 0; k < 4; ++k) sm.pack[t][k] = 0ull;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sm.ext[t][k] = 0ull;
+    }
+    if (t == 0) sm.abort = 0;
     __syncthreads();
     for (;;) {
-        if (t == 0) s_seg = s_abort ? 0xFFFFFFFFu : (uint32_t)atomicAdd(a.next, 1ull);
+        if (t == 0) {
+            sm.seg = sm.abort ? 0xFFFFFFFFu : (uint32_t)atomicAdd(a.next, 1ull);
+            sm.n_list = 0;
+        }
         __syncthreads();
-        const uint32_t g = s_seg;
+        const uint32_t g = sm.seg;
         if (g >= n_seg) break;
+        const unsigned long long tag = (unsigned long long)(g + 1) << 32;
+
+        if (poller) {
+            // ---------------- poll warp: external inputs still pending
+            __syncthreads();  // the executors have listed them
+            uint32_t n = sm.n_list;
+            uint32_t passes = 0;
+            while (n) {
+                if (*(volatile int *)&sm.abort) break;
+                if ((++passes & 15u) == 0 &&
+                    __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns)
+                    break;  // the executors see the budget run out themselves
+                uint32_t kept = 0, min_gap = 0xFFFFFFFFu;
+                bool any_new = false;
+                for (uint32_t base = 0; base < n; base += 128) {
+                    uint32_t sl[4], rs[4], tf[4];
+                    unsigned long long pv[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t i = base + 32 * j + lane;
+                        sl[j] = 0xFFFFFFFFu;
+                        if (i < n) {
+                            sl[j] = sm.list_slot[i];
+                            rs[j] = sm.list_res[i];
+                            tf[j] = sm.list_turn[i];
+                            pv[j] = ld_rlx64(o.packed + rs[j]);
+                        }
+                    }
+                    bool ok[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        ok[j] = false;
+                        if (sl[j] == 0xFFFFFFFFu) continue;
+                        const uint32_t c = (uint32_t)(pv[j] >> 32), need = tf[j] & kTurnMask;
+                        ok[j] = (tf[j] & kFWriter) ? c == need : c >= need;
+                        if (!ok[j]) {
+                            const uint32_t gp = need > c ? need - c : 1u;
+                            min_gap = min(min_gap, gp);
+                            atomicMin(&sm.gap[sl[j] >> 2], gp);
+                        }
+                    }
+                    if (__any_sync(kFull, ok[0] || ok[1] || ok[2] || ok[3])) {
+                        // acquire what the previous holders wrote before the
+                        // counters moved (cache sets), then hand the inputs on
+                        fence_gpu();
+                        any_new = true;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (ok[j])
+                            *(volatile unsigned long long *)&sm.ext[sl[j] >> 2][sl[j] & 3u] =
+                                tag | (uint32_t)pv[j];
+                    __syncwarp();
+                    // compact the pending entries in place (writes land below
+                    // every index this warp still has to read)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool keep = sl[j] != 0xFFFFFFFFu && !ok[j];
+                        const unsigned m = __ballot_sync(kFull, keep);
+                        if (keep) {
+                            const uint32_t p = kept + __popc(m & lanemask_lt());
+                            sm.list_slot[p] = sl[j];
+                            sm.list_res[p] = rs[j];
+                            sm.list_turn[p] = tf[j];
+                        }
+                        kept += __popc(m);
+                    }
+                    __syncwarp();
+                }
+                n = kept;
+                if (n && !any_new) {
+                    const uint32_t mg = __reduce_min_sync(kFull, min_gap);
+                    if (HETM_SLEEP_PER_TURN && mg > 8 && mg != 0xFFFFFFFFu)
+                        __nanosleep(min(mg * (uint32_t)HETM_SLEEP_PER_TURN, 8000u));
+                }
+            }
+            __syncthreads();  // end of segment
+            continue;
+        }
+
+        // ---------------- executor lanes
         const uint32_t r = g * SEG + t;
         OrdRec rc;
         uint32_t n = 0, wl = 0;
@@ -674,58 +786,76 @@ __global__ void __launch_bounds__(SEG) k_seg_exec(OrderArgs o) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (ext & (1u << k)) pv[k] = ld_rlx64(o.packed + rc.res[k]);
-        // Polls are paced per lane: a lane looks at its poll results (and
-        // polls again) only when its own back-off has expired, and the
-        // back-off grows with the number of turns still ahead of it, so lanes
-        // far from the front of the dependency chains rarely load the memory
-        // system.  Inside the wave loop only the work that a later
-        // transaction waits on is done (the shared-memory handoff and the
-        // publish to a later segment); everything else waits for the end.
-        long long next_check = clock64() + kPollCycles;
+        // one look at the external inputs; what is not there yet goes to the poll warp
+        uint32_t gap0 = 0xFFFFFFFFu;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!(ext & (1u << k))) continue;
+            const uint32_t c = (uint32_t)(pv[k] >> 32), need = rc.turn[k] & kTurnMask;
+            if ((rc.turn[k] & kFWriter) ? c == need : c >= need) {
+                ext &= ~(1u << k);
+                cur[k] = (int32_t)(uint32_t)pv[k];
+            } else {
+                gap0 = min(gap0, need > c ? need - c : 1u);
+            }
+        }
+        {
+            const uint32_t cnt = __popc(ext);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int w = 1; w < 32; w <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, w);
+                if (lane >= (unsigned)w) incl += y;
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            uint32_t base = 0;
+            if (lane == 31 && total) base = atomicAdd(&sm.n_list, total);
+            base = __shfl_sync(kFull, base, 31);
+            uint32_t p = base + incl - cnt;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!(ext & (1u << k))) continue;
+                sm.list_slot[p] = (t << 2) | (uint32_t)k;
+                sm.list_res[p] = rc.res[k];
+                sm.list_turn[p] = rc.turn[k];
+                ++p;
+            }
+        }
+        sm.gap[t] = gap0;
+        sm.eff[t] = ext ? gap0 : 0u;
+        __syncthreads();  // the pending list is complete: the poll warp starts
+
         bool finished = n == 0;
         bool executed = false;
         bool timed_out = false;
-        uint32_t waves = 0;
-        uint32_t dist = 0;  // turns still to go before this lane's nearest external turn
+        // Each slot still pending watches one shared word: its predecessor's
+        // output slot in this segment, or its external input from the poll
+        // warp; a slot no longer pending watches this lane's own output
+        // (never tagged before the lane runs).  One pass is four
+        // independent shared loads and selects, with no per-slot branching,
+        // so that a hand-on inside the segment costs one short pass.
+        uint32_t watch[4];
+        uint32_t pend = ext | loc;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned long long *w = &sm.pack[t][k];
+            if (loc & (1u << k)) w = &sm.pack[rc.src[k] >> 2][rc.src[k] & 3u];
+            else if (ext & (1u << k)) w = &sm.ext[t][k];
+            watch[k] = (uint32_t)__cvta_generic_to_shared(w);
+        }
+        uint32_t idle = 0, checks = 0;
         for (;;) {
-            if (__all_sync(kFull, finished)) break;
-            bool ready = false;
-            if (!finished) {
-                if (ext) {
-                    const long long now = clock64();
-                    if (now >= next_check) {
-                        dist = 0xFFFFFFFFu;
+            unsigned long long v[4];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            if (!(ext & (1u << k))) continue;
-                            const uint32_t c = (uint32_t)(pv[k] >> 32), need = rc.turn[k] & kTurnMask;
-                            if ((rc.turn[k] & kFWriter) ? c == need : c >= need) {
-                                ext &= ~(1u << k);
-                                cur[k] = (int32_t)(uint32_t)pv[k];
-                            } else {
-                                dist = min(dist, need > c ? need - c : 1u);
-                                pv[k] = ld_rlx64(o.packed + rc.res[k]);
-                            }
-                        }
-                        const uint32_t back = dist < 2048u ? dist * 32u : 65536u;
-                        next_check = now + kPollCycles + back;
-                        if (!ext) dist = 0;
-                    }
-                }
-                if (loc) {
+            for (int k = 0; k < 4; ++k)
+                asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v[k]) : "r"(watch[k]) : "memory");
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (!(loc & (1u << k))) continue;
-                        const unsigned long long pk =
-                            *(volatile unsigned long long *)&s_pack[rc.src[k] >> 2][rc.src[k] & 3u];
-                        if ((uint32_t)(pk >> 32) == g + 1) {
-                            cur[k] = (int32_t)(uint32_t)pk;
-                            loc &= ~(1u << k);
-                        }
-                    }
-                }
-                ready = (ext | loc) == 0;
+            for (int k = 0; k < 4; ++k) {
+                const bool got = ((pend >> k) & 1u) && (uint32_t)(v[k] >> 32) == g + 1;
+                cur[k] = got ? (int32_t)(uint32_t)v[k] : cur[k];
+                pend &= got ? ~(1u << k) : ~0u;
             }
+            const bool ready = !finished && pend == 0;
             if (ready && !cache) {
                 if (rmw4) {
                     sum = cur[0] + cur[1] + cur[2] + cur[3];
@@ -756,8 +886,7 @@ __global__ void __launch_bounds__(SEG) k_seg_exec(OrderArgs o) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (k < (int)n)
-                        *(volatile unsigned long long *)&s_pack[t][k] =
-                            ((unsigned long long)(g + 1) << 32) | (uint32_t)nv[k];
+                        *(volatile unsigned long long *)&sm.pack[t][k] = tag | (uint32_t)nv[k];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (k < (int)n && (rc.turn[k] & kFPublish))
@@ -766,6 +895,7 @@ __global__ void __launch_bounds__(SEG) k_seg_exec(OrderArgs o) {
                                      (uint32_t)nv[k]);
                 finished = true;
                 executed = true;
+                *(volatile uint32_t *)&sm.eff[t] = 0xFFFFFFFFu;
             } else if (ready) {  // cache request: holds or shares its set
                 const unsigned long long key = 2ull * (v0 + 1 + rc.u);
                 fence_gpu();  // acquire the set's previous holders' writes
@@ -777,20 +907,37 @@ __global__ void __launch_bounds__(SEG) k_seg_exec(OrderArgs o) {
                 if (o_out) static_cast<uint64_t *>(o_out)[rc.li] = out;
                 finished = true;
                 executed = true;
+                *(volatile uint32_t *)&sm.eff[t] = 0xFFFFFFFFu;
             }
             __syncwarp();
-            if (!__any_sync(kFull, ready)) {
-                if ((++waves & 15u) == 0 &&
-                    __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns) {
-                    timed_out = true;
-                    break;
-                }
-                // Idle warp: sleep in proportion to how far its nearest turn
-                // is, so that the warps at the front of the chains get the
-                // issue slots of the SM.
-                const uint32_t wd = __reduce_min_sync(kFull, finished ? 0xFFFFFFFFu : dist);
-                if (wd > 8 && wd != 0xFFFFFFFFu) __nanosleep(min(wd * 16u, 8000u));
+            if (__all_sync(kFull, finished)) break;
+            if (__any_sync(kFull, ready)) {
+                idle = 0;
+                continue;
             }
+            if (++idle < 8) continue;
+            // eight passes without progress: bookkeeping, then maybe sleep
+            idle = 0;
+            uint32_t dist = 0xFFFFFFFFu;
+            if (!finished) {
+                if (pend & ext) dist = *(volatile uint32_t *)&sm.gap[t];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!((pend & loc) & (1u << k))) continue;
+                    const uint32_t pe = *(volatile uint32_t *)&sm.eff[rc.src[k] >> 2];
+                    dist = min(dist, pe == 0xFFFFFFFFu ? 0u : pe + 1u);
+                }
+                *(volatile uint32_t *)&sm.eff[t] = dist;
+            }
+            if (__any_sync(kFull, *(volatile int *)&sm.abort != 0) ||
+                ((++checks & 3u) == 0 &&
+                 __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns)) {
+                timed_out = true;
+                break;
+            }
+            const uint32_t wd = __reduce_min_sync(kFull, finished ? 0xFFFFFFFFu : dist);
+            if (HETM_SLEEP_PER_TURN && wd > 8 && wd != 0xFFFFFFFFu)
+                __nanosleep(min(wd * (uint32_t)HETM_SLEEP_PER_TURN, 8000u));
         }
         if (executed) {
             const unsigned long long key = 2ull * (v0 + 1 + rc.u);
@@ -813,20 +960,20 @@ __global__ void __launch_bounds__(SEG) k_seg_exec(OrderArgs o) {
             if (o_status) o_status[rc.li] = kGaveUp;
             ++n_gaveup;
             set_err(a.err, kErrTimeout);
-            s_abort = 1;
+            sm.abort = 1;
             // release local successors so that they end too
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                *(volatile unsigned long long *)&s_pack[t][k] = (unsigned long long)(g + 1) << 32;
+            for (int k = 0; k < 4; ++k) *(volatile unsigned long long *)&sm.pack[t][k] = tag;
         }
-        __syncthreads();
+        __syncthreads();  // end of segment
     }
+    if (poller) return;
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1) {
         n_commit += __shfl_xor_sync(kFull, n_commit, w);
         n_gaveup += __shfl_xor_sync(kFull, n_gaveup, w);
     }
-    if ((t & 31u) == 0) {
+    if (lane == 0) {
         if (n_commit) atomicAdd(a.counters + 0, n_commit);
         if (n_gaveup) atomicAdd(a.counters + 1, n_gaveup);
     }
@@ -853,19 +1000,32 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
     e = cudaMemsetAsync(o.e.next, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     switch (o.seg_log2) {
-    case 7: k_seg_exec<128><<<exec_blocks, 128, 0, s>>>(o); break;
-    case 8: k_seg_exec<256><<<exec_blocks, 256, 0, s>>>(o); break;
-    case 9: k_seg_exec<512><<<exec_blocks, 512, 0, s>>>(o); break;
+    case 7: k_seg_exec<128><<<exec_blocks, 128 + 32, sizeof(SegSmem<128>), s>>>(o); break;
+    case 8: k_seg_exec<256><<<exec_blocks, 256 + 32, sizeof(SegSmem<256>), s>>>(o); break;
+    case 9: k_seg_exec<512><<<exec_blocks, 512 + 32, sizeof(SegSmem<512>), s>>>(o); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+namespace {
+template <uint32_t SEG>
+int seg_occupancy(int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_seg_exec<SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(SegSmem<SEG>));
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec<SEG>, SEG + 32,
+                                                              sizeof(SegSmem<SEG>));
+}
+}  // namespace
+
+// Also raises the kernels' dynamic shared-memory limit; called once per
+// context before the first launch.
 int ordered_exec_occupancy(uint32_t seg, int *blocks_per_sm) {
     switch (seg) {
-    case 128: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec<128>, 128, 0);
-    case 256: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec<256>, 256, 0);
-    case 512: return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_seg_exec<512>, 512, 0);
+    case 128: return seg_occupancy<128>(blocks_per_sm);
+    case 256: return seg_occupancy<256>(blocks_per_sm);
+    case 512: return seg_occupancy<512>(blocks_per_sm);
     default: return (int)cudaErrorInvalidValue;
     }
 }

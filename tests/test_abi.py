@@ -68,3 +68,10 @@ def test_autotune_space_and_argument_checks_without_gpu():
     rc = h.lib().hetm_autotune(1 << 10, None, None, 0, None, 0, None, None, ctypes.byref(best),
                                ctypes.byref(g), None, 0, None)
     assert rc == h.HETM_EINVAL
+
+
+def test_handoff_probe_rejects_bad_arguments_without_gpu():
+    import paper_1905_00661_b300 as h
+    g = ctypes.c_double()
+    assert h.lib().hetm_handoff_latency(0, ctypes.byref(g), None) == h.HETM_EINVAL
+    assert h.lib().hetm_handoff_latency(100, None, None) == h.HETM_EINVAL

@@ -78,3 +78,12 @@ def test_autotune_picks_best_and_avoids_false_conflicts(hetm):
         assert ref.n_conflicts == 0
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_W), ref.final)
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_S), ref.final)
+
+
+def test_handoff_latency_probe(hetm):
+    """Hand-on of a word: through shared memory (two warps of a CTA) well under
+    a microsecond, and no slower than across two SMs through L2."""
+    g, sh = hetm.handoff_latency(5000)
+    assert 5.0 < sh < 2000.0
+    assert 20.0 < g < 20000.0
+    assert sh < g
