@@ -613,13 +613,20 @@ __device__ void cache_request(const ExecArgs &a, const hetm_cache_req &r, uint32
 // warp, and with it the lanes at the front of a chain, for an L2 round trip
 // at every wave.  Instead each lane checks its external inputs once when the
 // segment starts, and the poll warp polls the ones still pending and hands
-// each one over through shared memory as soon as it is satisfied.  Idle
-// warps sleep in proportion to how far their nearest lane is from its turn
-// (the poll warp records the gap of external waits; a local wait is one more
-// than its predecessor's), so that the warps at the front of the chains get
-// the issue slots.
+// each one over through shared memory as soon as it is satisfied.  A warp
+// none of whose lanes ran in a pass sleeps briefly, leaving the issue slots
+// to the warps at the front of the chains.  (Measured on the 4M-transaction
+// Zipf(0.99) batch: 50 ns after each idle pass is a few percent faster than
+// spinning; longer sleeps, or sleeps scaled by an estimate of the turns still
+// ahead, are no better.)
 #ifndef HETM_SLEEP_PER_TURN
-#define HETM_SLEEP_PER_TURN 32  // ns of sleep per turn still ahead of an idle warp
+#define HETM_SLEEP_PER_TURN 32  // poll warp: ns of sleep per turn still ahead of its nearest wait
+#endif
+#ifndef HETM_IDLE_SLEEP_NS
+#define HETM_IDLE_SLEEP_NS 50  // ns of sleep after a pass in which no lane of the warp ran
+#endif
+#ifndef HETM_IDLE_PASSES
+#define HETM_IDLE_PASSES 4  // idle passes between two looks at the abort flag and the clock
 #endif
 
 template <uint32_t SEG>
@@ -631,8 +638,6 @@ struct SegSmem {
     uint32_t list_slot[SEG * 4];      // pending external slots: t << 2 | k
     uint32_t list_res[SEG * 4];       //   their resource
     uint32_t list_turn[SEG * 4];      //   their turn word
-    uint32_t gap[SEG];                // min turns still ahead over the lane's external waits
-    uint32_t eff[SEG];                // the lane's distance estimate, for its local successors
     uint32_t seg, n_list;
     int abort;
 };
@@ -701,11 +706,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                         if (sl[j] == 0xFFFFFFFFu) continue;
                         const uint32_t c = (uint32_t)(pv[j] >> 32), need = tf[j] & kTurnMask;
                         ok[j] = (tf[j] & kFWriter) ? c == need : c >= need;
-                        if (!ok[j]) {
-                            const uint32_t gp = need > c ? need - c : 1u;
-                            min_gap = min(min_gap, gp);
-                            atomicMin(&sm.gap[sl[j] >> 2], gp);
-                        }
+                        if (!ok[j]) min_gap = min(min_gap, need > c ? need - c : 1u);
                     }
                     if (__any_sync(kFull, ok[0] || ok[1] || ok[2] || ok[3])) {
                         // acquire what the previous holders wrote before the
@@ -787,7 +788,6 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         for (int k = 0; k < 4; ++k)
             if (ext & (1u << k)) pv[k] = ld_rlx64(o.packed + rc.res[k]);
         // one look at the external inputs; what is not there yet goes to the poll warp
-        uint32_t gap0 = 0xFFFFFFFFu;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (!(ext & (1u << k))) continue;
@@ -795,8 +795,6 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             if ((rc.turn[k] & kFWriter) ? c == need : c >= need) {
                 ext &= ~(1u << k);
                 cur[k] = (int32_t)(uint32_t)pv[k];
-            } else {
-                gap0 = min(gap0, need > c ? need - c : 1u);
             }
         }
         {
@@ -821,8 +819,6 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 ++p;
             }
         }
-        sm.gap[t] = gap0;
-        sm.eff[t] = ext ? gap0 : 0u;
         __syncthreads();  // the pending list is complete: the poll warp starts
 
         bool finished = n == 0;
@@ -895,7 +891,6 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                                      (uint32_t)nv[k]);
                 finished = true;
                 executed = true;
-                *(volatile uint32_t *)&sm.eff[t] = 0xFFFFFFFFu;
             } else if (ready) {  // cache request: holds or shares its set
                 const unsigned long long key = 2ull * (v0 + 1 + rc.u);
                 fence_gpu();  // acquire the set's previous holders' writes
@@ -907,7 +902,6 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 if (o_out) static_cast<uint64_t *>(o_out)[rc.li] = out;
                 finished = true;
                 executed = true;
-                *(volatile uint32_t *)&sm.eff[t] = 0xFFFFFFFFu;
             }
             __syncwarp();
             if (__all_sync(kFull, finished)) break;
@@ -915,29 +909,16 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 idle = 0;
                 continue;
             }
-            if (++idle < 8) continue;
-            // eight passes without progress: bookkeeping, then maybe sleep
+            // an idle pass leaves the issue slots to the warps that can run
+            if (HETM_IDLE_SLEEP_NS) __nanosleep(HETM_IDLE_SLEEP_NS);
+            if (++idle < HETM_IDLE_PASSES) continue;
             idle = 0;
-            uint32_t dist = 0xFFFFFFFFu;
-            if (!finished) {
-                if (pend & ext) dist = *(volatile uint32_t *)&sm.gap[t];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (!((pend & loc) & (1u << k))) continue;
-                    const uint32_t pe = *(volatile uint32_t *)&sm.eff[rc.src[k] >> 2];
-                    dist = min(dist, pe == 0xFFFFFFFFu ? 0u : pe + 1u);
-                }
-                *(volatile uint32_t *)&sm.eff[t] = dist;
-            }
             if (__any_sync(kFull, *(volatile int *)&sm.abort != 0) ||
                 ((++checks & 3u) == 0 &&
                  __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns)) {
                 timed_out = true;
                 break;
             }
-            const uint32_t wd = __reduce_min_sync(kFull, finished ? 0xFFFFFFFFu : dist);
-            if (HETM_SLEEP_PER_TURN && wd > 8 && wd != 0xFFFFFFFFu)
-                __nanosleep(min(wd * (uint32_t)HETM_SLEEP_PER_TURN, 8000u));
         }
         if (executed) {
             const unsigned long long key = 2ull * (v0 + 1 + rc.u);
