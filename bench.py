@@ -325,6 +325,7 @@ def bench_round_at_scale(torch, h, v, reps=5):
             "apply_ms": ms_a, "apply_gbs": (12 * n + 8 * n_win) / (ms_a * 1e-3) / 1e9,
             "merge_ms": ms_m, "dirty_chunks": dirty,
             "merge_gbs": 2 * dirty * chunk / (ms_m * 1e-3) / 1e9,
+            "apply_reads": n, "apply_writes": 2 * n_win,
         }
     return out
 
@@ -359,7 +360,16 @@ def bench_w1_uniform(torch, h, init, update_frac, reps=3):
     e = float(np.median(ms))
     upd = int(tx["flags"].sum())
     return {"update_frac": update_frac, "exec_ms": e, "tx_per_s": N_TX / (e * 1e-3),
-            "exec_gbs": (16 * N_TX + 16 * upd) / (e * 1e-3) / 1e9}
+            "exec_gbs": (16 * N_TX + 16 * upd) / (e * 1e-3) / 1e9,
+            "word_reads": 4 * N_TX, "word_writes": 4 * upd}
+
+
+def random_bound(rec, ra, t_ms):
+    """Random-sector roofline of scattered work: every word access is one
+    32-byte sector at the probed random read / write rate."""
+    r, w = ra
+    b = (rec["reads"] / r + rec["writes"] / w) * 1e3
+    return {"bound_ms": b, "frac": b / t_ms}
 
 
 def bench_cache(torch, h, n_batches=24, seed=6):
@@ -589,7 +599,14 @@ def main():
     import paper_1905_00661_b300 as h
     chain = [critical_path(b) for b in inputs[1]]
     handoff_g, handoff_s = h.handoff_latency(20000)
+    ra = h.random_access_rate(LOG2W, 1 << 28)
     w1 = [bench_w1_uniform(torch, h, inputs[0], f) for f in (0.1, 1.0)]
+    for x in w1:
+        x["random_roofline"] = random_bound({"reads": x.pop("word_reads"),
+                                             "writes": x.pop("word_writes")}, ra, x["exec_ms"])
+    for x in res["val"]["round"].values():
+        x["apply_random_roofline"] = random_bound({"reads": x.pop("apply_reads"),
+                                                   "writes": x.pop("apply_writes")}, ra, x["apply_ms"])
     cache = bench_cache(torch, h)
     sv_in = serving_inputs(args.serve_batches)
     rates = [SERVE_RATE, 5 * SERVE_RATE, 25 * SERVE_RATE]
@@ -634,7 +651,12 @@ def main():
                   # serialization-depth bound: every step of the longest chain
                   # costs at least one hand-on (all inside CTAs: the floor)
                   "bound_ms": float(np.mean(chain)) * handoff_s * 1e-6,
-                  "frac_of_bound": float(np.mean(chain)) * handoff_s * 1e-6 / exec_ms},
+                  "frac_of_bound": float(np.mean(chain)) * handoff_s * 1e-6 / exec_ms,
+                  "random_roofline": random_bound(
+                      {"reads": 4 * N_TX,
+                       "writes": 4 * float(np.mean([int(b["flags"].sum()) for b in inputs[1]]))},
+                      ra, exec_ms)},
+        "random_access_per_s": {"read": ra[0], "write": ra[1], "array_words": 1 << LOG2W},
         "w1_uniform": w1,
         "cache": cache,
         "validation": {"kernel": "k_validate_direct", "ms": val["ms"], "gbs": val["gbs"],

@@ -376,6 +376,17 @@ HETM_API void hetm_server_destroy(hetm_server *s);
  * HETM_ETIMEOUT if one gave up. */
 HETM_API int hetm_handoff_latency(uint32_t rounds, double *global_ns, double *shared_ns);
 
+/* Random-sector rate of the current device: n_access random 4-byte reads
+ * (*read_per_s) and writes (*write_per_s) spread over a 2^log2_words-word
+ * array (20 <= log2_words <= 32; choose it larger than L2 so that every
+ * access is a DRAM sector), eight in flight per thread, timed with CUDA
+ * events after one warm-up pass.  This is the roofline of scattered work:
+ * the executor's word accesses and the apply's timestamp probes and winner
+ * writes.  Allocates and frees the array; synchronous.  Either pointer may
+ * be NULL, not both. */
+HETM_API int hetm_random_access_rate(uint32_t log2_words, uint64_t n_access, double *read_per_s,
+                                     double *write_per_s);
+
 /* ------------------------------------------------------------ autotuner */
 /* The paper runs one executor shape and studies the conflict granule (Sec.
  * V-A: 4 B against 1 KB granules, instrumentation cost against false

@@ -70,7 +70,7 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_round_wait", "hetm_server_config_default", "hetm_server_create",
            "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
            "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune",
-           "hetm_handoff_latency")
+           "hetm_handoff_latency", "hetm_random_access_rate")
 
 
 class hetm_tune_space(ctypes.Structure):
@@ -148,6 +148,7 @@ def _declare(L):
         "hetm_server_destroy": (None, [_vp]),
         "hetm_tune_space_default": (_int, [P(hetm_tune_space)]),
         "hetm_handoff_latency": (_int, [_u32, P(ctypes.c_double), P(ctypes.c_double)]),
+        "hetm_random_access_rate": (_int, [_u32, _u64, P(ctypes.c_double), P(ctypes.c_double)]),
         "hetm_autotune": (_int, [_u64, _vp, P(hetm_batch), _u32, _vp, _u64, P(hetm_config),
                                  P(hetm_tune_space), P(hetm_config), P(_u32), P(hetm_tune_trial),
                                  _u32, P(_u32)]),
@@ -241,6 +242,14 @@ def handoff_latency(rounds=20000):
     _ck(_lib.hetm_handoff_latency(int(rounds), ctypes.byref(g), ctypes.byref(sh)),
         "hetm_handoff_latency")
     return g.value, sh.value
+
+
+def random_access_rate(log2_words=28, n_access=1 << 28):
+    """(random 4-byte reads/s, writes/s) over a 2^log2_words-word array (hetm_random_access_rate)."""
+    r, w = ctypes.c_double(), ctypes.c_double()
+    _ck(_lib.hetm_random_access_rate(int(log2_words), int(n_access), ctypes.byref(r), ctypes.byref(w)),
+        "hetm_random_access_rate")
+    return r.value, w.value
 
 
 _TUNED = ("exec_mode", "exec_threads", "exec_blocks", "lock_log2", "ws_chunk_bytes")

@@ -1,4 +1,7 @@
-// Handoff-latency probe: the floor under one step of a chain of conflicting
+// Hardware probes that give the rooflines of the latency- and scatter-bound
+// kernels (the memory-copy and GEMM peaks do not describe them).
+//
+// Handoff latency: the floor under one step of a chain of conflicting
 // transactions.  Committing transactions in a fixed order serializes every
 // word's writers, so a batch cannot finish faster than its longest chain of
 // conflicting transactions times the time one transaction takes to hand a
@@ -87,10 +90,83 @@ __global__ void k_handoff_shared(uint32_t rounds, unsigned long long *out_ns, in
     if (me == 0) out_ns[0] = globaltimer_ns() - t0;
 }
 
+// Random 4-byte accesses over an array larger than L2: every access touches
+// its own 32-byte sector, so accesses/s is the random-sector rate that bounds
+// scattered work (the executor's word reads and writes, the apply's TS
+// probes and winner writes).  Addresses come from a counter hash; eight
+// accesses per thread are in flight at once.
+__device__ __forceinline__ uint64_t probe_addr(uint64_t i, uint64_t mask) {
+    return splitmix_fin(i * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull) & mask;
+}
+
+__global__ void k_gather(const int32_t *__restrict__ x, uint64_t mask, uint64_t n, int32_t *sink) {
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    int32_t acc = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += 8 * stride) {
+        int32_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint64_t k = i + j * stride;
+            v[j] = k < n ? __ldcg(x + probe_addr(k, mask)) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc ^= v[j];
+    }
+    if (acc == 0x7FFFFFFF) *sink = acc;  // keeps the loads
+}
+
+__global__ void k_scatter(int32_t *x, uint64_t mask, uint64_t n) {
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        x[probe_addr(i, mask)] = (int32_t)i;
+}
+
 }  // namespace
 }  // namespace hetm
 
 using namespace hetm;
+
+extern "C" int hetm_random_access_rate(uint32_t log2_words, uint64_t n_access, double *read_per_s,
+                                       double *write_per_s) {
+    if (log2_words < 20 || log2_words > 32 || n_access == 0 || (!read_per_s && !write_per_s))
+        return HETM_EINVAL;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HETM_ECUDA;
+    const uint64_t words = 1ull << log2_words;
+    int32_t *x = nullptr;
+    if (cudaMalloc(&x, words * 4 + 64) != cudaSuccess) return HETM_ENOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemset(x, 0, words * 4 + 64);
+    const int blocks = n_sm * 8;
+    float ms = 0;
+    for (int rep = 0; e == cudaSuccess && rep < 2; ++rep) {  // first pass warms up
+        if (read_per_s) {
+            e = cudaEventRecord(e0);
+            k_gather<<<blocks, 256>>>(x, words - 1, n_access, x + words);
+            if (e == cudaSuccess) e = cudaEventRecord(e1);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && rep) *read_per_s = n_access / (ms * 1e-3);
+        }
+        if (e == cudaSuccess && write_per_s) {
+            e = cudaEventRecord(e0);
+            k_scatter<<<blocks, 256>>>(x, words - 1, n_access);
+            if (e == cudaSuccess) e = cudaEventRecord(e1);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && rep) *write_per_s = n_access / (ms * 1e-3);
+        }
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(x);
+    return e == cudaSuccess ? HETM_OK : HETM_ECUDA;
+}
 
 extern "C" int hetm_handoff_latency(uint32_t rounds, double *global_ns, double *shared_ns) {
     if (rounds == 0 || rounds > (1u << 24) || (!global_ns && !shared_ns)) return HETM_EINVAL;

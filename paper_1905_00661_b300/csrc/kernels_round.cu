@@ -92,6 +92,17 @@ __device__ __forceinline__ uint32_t probe(const uint32_t *rs, const uint32_t *fl
     return (__ldg(rs + (g >> 5)) >> (g & 31)) & 1u;
 }
 
+// Raise TS[a] to s.  A skewed log sends many tuples to a few hot words, and
+// atomics on one word serialize in its L2 slice; a tuple whose timestamp is
+// not above the value seen through L1 cannot change TS and skips the atomic.
+// TS only grows during the pass, so a stale cached value is at most the
+// current one: a skip is always safe, at worst an atomic is not saved.
+__device__ __forceinline__ void ts_raise(uint32_t *ts, uint32_t a, uint32_t s) {
+    uint32_t seen;
+    asm volatile("ld.global.ca.u32 %0, [%1];" : "=r"(seen) : "l"(ts + a));
+    if (seen < s) atomicMax(ts + a, s);
+}
+
 // Validation (Sec. IV-C): flag = RS_bmp[granule(addr)] for every tuple, the
 // flags bit-packed in log order, the hits counted.  kMax additionally raises
 // TS[addr] to the tuple's timestamp (first pass of the apply).
@@ -123,7 +134,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
         for (int j = 0; j < 4; ++j) {
             if (a[j] < n_words) {
                 nib |= probe(rs, flt, a[j], gshift) << j;
-                if (kMax) atomicMax(ts + a[j], s[j]);
+                if (kMax) ts_raise(ts, a[j], s[j]);
             } else {
                 bad = true;
             }
@@ -145,7 +156,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
                 uint32_t a = log[i].addr;
                 if (a < n_words) {
                     bit = probe(rs, flt, a, gshift);
-                    if (kMax) atomicMax(ts + a, log[i].ts);
+                    if (kMax) ts_raise(ts, a, log[i].ts);
                 } else {
                     bad = true;
                 }

@@ -75,3 +75,11 @@ def test_handoff_probe_rejects_bad_arguments_without_gpu():
     g = ctypes.c_double()
     assert h.lib().hetm_handoff_latency(0, ctypes.byref(g), None) == h.HETM_EINVAL
     assert h.lib().hetm_handoff_latency(100, None, None) == h.HETM_EINVAL
+
+
+def test_random_access_probe_rejects_bad_arguments_without_gpu():
+    import paper_1905_00661_b300 as h
+    r = ctypes.c_double()
+    assert h.lib().hetm_random_access_rate(10, 100, ctypes.byref(r), None) == h.HETM_EINVAL
+    assert h.lib().hetm_random_access_rate(24, 0, ctypes.byref(r), None) == h.HETM_EINVAL
+    assert h.lib().hetm_random_access_rate(24, 100, None, None) == h.HETM_EINVAL

@@ -87,3 +87,9 @@ def test_handoff_latency_probe(hetm):
     assert 5.0 < sh < 2000.0
     assert 20.0 < g < 20000.0
     assert sh < g
+
+
+def test_random_access_probe(hetm):
+    """Random 4-byte reads and writes over 1 GiB: between 1e9 and 1e12 per second."""
+    r, w = hetm.random_access_rate(28, 1 << 26)
+    assert 1e9 < r < 1e12 and 1e9 < w < 1e12
