@@ -36,8 +36,8 @@ import workloads as wl  # noqa: E402
 
 # DRAM bytes (read + write) of the ordered-phase kernel per transaction of the
 # round, from one ncu capture of `bench.py --case rmw_small` (1M transactions,
-# 35.4 MB + 498.2 MB), scaled to a launch by the transaction count.
-TRAFFIC_SEG_EXEC_PER_TX = (35.4e6 + 498.2e6) / (1 << 20)
+# 36.6 MB + 0.6 MB), scaled to a launch by the transaction count.
+TRAFFIC_SEG_EXEC_PER_TX = (36.641e6 + 0.626e6) / (1 << 20)
 # autotuner search space of the main step (both executors, three CTA sizes,
 # the granules of Sec. V-A's study and three merge chunks)
 TUNE_SPACE = {"modes": 3, "threads": [128, 256, 512], "blocks_per_sm": [0],
@@ -534,6 +534,21 @@ def run_case(name):
             torch.cuda.synchronize()
         print(json.dumps({"case": name, "hits": int(cnt.item()), "expected": v.n_hits_planted}))
         return 0 if int(cnt.item()) == v.n_hits_planted else 1
+    if name == "sync_small":  # validate + TS max, apply, merge of the at-scale log, 2^27 words
+        v = wl.validation_round(seed=1, log2_words=27, granule_bytes=64, with_init=False)
+        wpg = 16
+        with h.Context(1 << 27, 64, {"log_capacity": 1 << 12, "cpu_threads": 1}) as ctx:
+            ctx.load(torch.zeros(1 << 27, dtype=torch.int32, device="cuda"))
+            first = torch.from_numpy((v.read_granules.astype(np.uint64) * wpg).astype(np.uint32)).cuda()
+            ctx.gpu_mark(first)
+            ctx.gpu_mark(torch.from_numpy(v.plant_addr).cuda(), torch.from_numpy(v.plant_value).cuda())
+            dlog = torch.from_numpy(v.log.view(np.uint8)).cuda()
+            ctx.log_attach(dlog, len(v.log))
+            st = ctx.round(stats=True)
+        print(json.dumps({"case": name, "n_conflicts": st["n_conflicts"], "expected": v.n_hits_planted,
+                          "ms_validate": st["ms_validate"], "ms_apply": st["ms_apply"],
+                          "ms_merge": st["ms_merge"], "rc": st["rc"]}))
+        return 0 if st["rc"] == h.HETM_OK and st["n_conflicts"] == v.n_hits_planted else 1
     raise SystemExit(f"unknown case {name}")
 
 
