@@ -134,7 +134,13 @@ typedef struct hetm_config {
     uint32_t cache_log2_sets;  /* object-cache layout (HETM_WL_CACHE)      */
     uint64_t cache_key_base, cache_val_base, cache_lru_base, cache_ver_base;
     uint32_t exec_mode;        /* HETM_EXEC_ORDERED (default) or HETM_EXEC_OPTIMISTIC */
-    uint32_t reserved0;
+    uint32_t early_validate;   /* 1: early validation (Sec. IV-D) in hetm_round --
+                                  while the ordered executor runs, a watcher
+                                  kernel re-scans the round's CPU log against
+                                  RS_bmp as commits set its bits; a hit stops
+                                  the execution phase (the round is lost to the
+                                  CPU anyway under GPU-loses).  Ordered mode,
+                                  fused rounds only; 0                        */
     uint64_t max_round_tx;     /* ordered mode: transactions per execution phase; 1<<22 */
     /* Optional device allocator (e.g. a framework's caching allocator);
      * NULL = cudaMalloc/cudaFree.  Called only from hetm_init/hetm_destroy. */
@@ -190,13 +196,15 @@ HETM_API void *hetm_ctx_stream(hetm_ctx *ctx);
  * STMR^W and every output (property P1, Sec. III).  An update commit has
  * key 2v (v = its commit version, unique); a read-only commit has key
  * 2v'+1 where v' is the newest version it observed.  status[i] = 1
- * committed, 2 gave up after max_attempts (no effect, no bitmap bits). */
+ * committed, 2 gave up after max_attempts (no effect, no bitmap bits), 3
+ * not run: early validation found a conflict and stopped the execution
+ * phase (the round rolls the whole batch back). */
 typedef struct hetm_batch {
     uint32_t workload;   /* HETM_WL_* */
     uint32_t n_tx;
     const void *tx;      /* n_tx records of the workload's type            */
     uint64_t *order;     /* out: commit key per transaction                */
-    uint8_t *status;     /* out: 1 committed, 2 gave up                    */
+    uint8_t *status;     /* out: 1 committed, 2 gave up, 3 not run         */
     void *out;           /* out: int32 (RMW) or uint64 (cache) per tx      */
     uint32_t txid_base;  /* RMW: txid = txid_base + index                   */
     uint32_t word_base;  /* BANK: account a is word word_base + a           */
@@ -302,7 +310,7 @@ typedef struct hetm_round_stats {
     uint32_t n_batches;      /* batches executed this round               */
     float ms_exec, ms_validate, ms_apply, ms_merge, ms_total;
     uint32_t n_kernels;      /* kernel launches this round (graph kernel nodes) */
-    uint32_t reserved;
+    uint32_t stopped_early;  /* 1: early validation stopped the execution phase */
 } hetm_round_stats;
 
 /* One whole round: run the queued batches (persistent executor), ship the

@@ -40,7 +40,7 @@ class hetm_config(ctypes.Structure):
                 ("cpu_threads", _u32), ("log_chunk_bytes", _u32), ("log_capacity", _u64),
                 ("cpu_log_capacity", _u64), ("max_batches", _u32), ("cache_log2_sets", _u32),
                 ("cache_key_base", _u64), ("cache_val_base", _u64), ("cache_lru_base", _u64),
-                ("cache_ver_base", _u64), ("exec_mode", _u32), ("reserved0", _u32),
+                ("cache_ver_base", _u64), ("exec_mode", _u32), ("early_validate", _u32),
                 ("max_round_tx", _u64), ("dev_alloc", _ALLOC), ("dev_free", _FREE),
                 ("alloc_user", _vp)]
 
@@ -55,7 +55,7 @@ class hetm_round_stats(ctypes.Structure):
                 ("committed", _u64), ("gave_up", _u64), ("aborts", _u64), ("dirty_chunks", _u64),
                 ("n_batches", _u32), ("ms_exec", ctypes.c_float), ("ms_validate", ctypes.c_float),
                 ("ms_apply", ctypes.c_float), ("ms_merge", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("n_kernels", _u32), ("reserved", _u32)]
+                ("ms_total", ctypes.c_float), ("n_kernels", _u32), ("stopped_early", _u32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -24,6 +24,8 @@ using namespace hetm;
 
 namespace {
 
+constexpr unsigned long long kWatchBudgetNs = 20ull * 1000 * 1000 * 1000;  // as the executor's
+
 struct Scratch {                    // device-resident counters
     unsigned long long gv;          // commit-version clock
     unsigned long long next;        // executor work counter
@@ -32,6 +34,10 @@ struct Scratch {                    // device-resident counters
     unsigned long long dirty;       // chunks merged by the last merge
     int err;
     int pad;
+    unsigned int stop;              // early validation: conflict seen, stop executing
+    unsigned int segs_done;         //   ordered-phase segments finished
+    unsigned int segs_total;        //   their number + 1 (0 = not known yet)
+    unsigned int pad2;
 };
 
 struct RoundOut {                   // pinned copy of the round's results
@@ -39,7 +45,7 @@ struct RoundOut {                   // pinned copy of the round's results
     unsigned long long conflicts;
     unsigned long long dirty;
     int err;
-    int pad;
+    unsigned int stopped;           // early validation stopped the execution phase
 };
 
 struct ThreadLog {
@@ -110,6 +116,10 @@ struct hetm_ctx {
     cudaGraphExec_t g_exec = nullptr, g_sync = nullptr;
     uint32_t n_kern[2] = {0, 0};  // kernel nodes of g_exec / g_sync
     cudaEvent_t ev[7] = {};  // round timing: 0/6 around the executor, 1..4 in the sync graph, 5 end
+    // early validation: watcher stream, "stop flag reset" node of g_exec, watcher done
+    bool early = false;
+    cudaStream_t watch = nullptr;
+    cudaEvent_t ev_watch_start = nullptr, ev_watch_done = nullptr;
 
     OrderArgs ord{};               // ordered-executor scratch (exec_mode ORDERED)
     int ord_blocks = 0;
@@ -277,6 +287,11 @@ ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
     a.budget_ns = 20ull * 1000 * 1000 * 1000;
     a.counters = c->scr->counters;
     a.err = &c->scr->err;
+    if (c->early) {
+        a.stop = &c->scr->stop;
+        a.segs_done = &c->scr->segs_done;
+        a.segs_total = &c->scr->segs_total;
+    }
     a.cache_log2_sets = c->cfg.cache_log2_sets;
     a.key_base = c->cfg.cache_key_base;
     a.val_base = c->cfg.cache_val_base;
@@ -287,16 +302,25 @@ ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
 
 // Executor launch(es) for the staged table: one persistent launch over all
 // batches, or one launch per batch.
-int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb) {
+// `capturing`: recorded into g_exec, which then marks (ev_watch_start) the
+// point where the early-validation stop flag has been cleared.
+int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = false) {
     if (c->cfg.exec_mode == HETM_EXEC_ORDERED) {
         OrderArgs o = c->ord;
         if (!per_batch) {
             o.e = exec_args(c, c->d_round, c->d_batches, c->d_prefix);
+            if (c->early) {
+                CK(cudaMemsetAsync(&c->scr->stop, 0, 3 * sizeof(unsigned int), c->stream));
+                if (capturing)
+                    CK(cudaEventRecordWithFlags(c->ev_watch_start, c->stream, cudaEventRecordExternal));
+            }
             CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream));
             return HETM_OK;
         }
         for (uint32_t b = 0; b < nb; ++b) {
             o.e = exec_args(c, c->d_round + 1 + b, c->d_batches + b, c->d_prefix0);
+            o.e.stop = nullptr;  // no watcher runs beside per-batch launches
+            o.e.segs_done = o.e.segs_total = nullptr;
             CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream));
         }
         return HETM_OK;
@@ -331,16 +355,18 @@ int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e) {
     CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal));
-    CK(cudaMemcpyAsync(c->out, c->scr->counters, sizeof(RoundOut) - sizeof(int) * 2,
+    CK(cudaMemcpyAsync(c->out, c->scr->counters, 5 * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(&c->out->err, &c->scr->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&c->out->stopped, &c->scr->stop, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                       c->stream));
     return HETM_OK;
 }
 
 int capture(hetm_ctx *c, cudaGraphExec_t *out, int which) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = which == 0 ? enqueue_exec(c, false, 0) : enqueue_sync(c, nullptr, -1, c->ev + 1);
+    int rc = which == 0 ? enqueue_exec(c, false, 0, true) : enqueue_sync(c, nullptr, -1, c->ev + 1);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc != HETM_OK) {
         if (g) cudaGraphDestroy(g);
@@ -426,6 +452,10 @@ void hetm_destroy(hetm_ctx *c) {
         if (c->tlog_free[i]) cudaEventDestroy(c->tlog_free[i]);
     }
     if (c->ship_done) cudaEventDestroy(c->ship_done);
+    if (c->watch) cudaStreamSynchronize(c->watch);
+    if (c->ev_watch_start) cudaEventDestroy(c->ev_watch_start);
+    if (c->ev_watch_done) cudaEventDestroy(c->ev_watch_done);
+    if (c->watch) cudaStreamDestroy(c->watch);
     for (auto &L : c->tlogs)
         for (auto *b : L->buf)
             if (b) cudaFreeHost(b);
@@ -489,6 +519,11 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         c->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&c->ship, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(HETM_ECUDA);
+    c->early = d.early_validate != 0 && d.exec_mode == HETM_EXEC_ORDERED;
+    if (c->early && (cudaStreamCreateWithFlags(&c->watch, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&c->ev_watch_start, cudaEventDisableTiming) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&c->ev_watch_done, cudaEventDisableTiming) != cudaSuccess))
         return fail(HETM_ECUDA);
 
     const uint32_t nb = d.max_batches;
@@ -807,6 +842,16 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
     if (rc != HETM_OK) return rc;
     rc = stage_round(c, log, n);
     if (rc != HETM_OK) return rc;
+    if (c->early && nb && n) {
+        // the watcher starts once the stop flag is clear and the log is on the
+        // device, runs beside the executor, and the sync phase waits for it
+        CK(cudaStreamWaitEvent(c->watch, c->ev_watch_start, 0));
+        CK(cudaStreamWaitEvent(c->watch, c->ship_done, 0));
+        CK(launch_watch(log, n, c->rs, c->gshift, c->n_words, &c->scr->stop, &c->scr->segs_done,
+                        &c->scr->segs_total, kWatchBudgetNs, c->n_sm, c->watch));
+        CK(cudaEventRecord(c->ev_watch_done, c->watch));
+        CK(cudaStreamWaitEvent(c->stream, c->ev_watch_done, 0));
+    }
     CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
     CK(cudaGraphLaunch(c->g_sync, c->stream));
     CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
@@ -841,7 +886,8 @@ int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     std::memcpy(c->prev_counters, c->out->counters, sizeof(c->prev_counters));
     stats->dirty_chunks = c->out->dirty;
     stats->n_batches = nb;
-    stats->n_kernels = (nb ? c->n_kern[0] : 0) + c->n_kern[1];
+    stats->n_kernels = (nb ? c->n_kern[0] : 0) + c->n_kern[1] + (c->early && nb && n ? 1u : 0u);
+    stats->stopped_early = c->early && nb && n ? c->out->stopped : 0u;
     float ms = 0;
     if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[6]) == cudaSuccess) stats->ms_exec = ms;
     if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) stats->ms_validate = ms;

@@ -10,6 +10,7 @@ namespace hetm {
 
 constexpr uint8_t kCommitted = 1;
 constexpr uint8_t kGaveUp = 2;
+constexpr uint8_t kNotRun = 3;  // the execution phase stopped early (early validation)
 constexpr unsigned kFull = 0xffffffffu;
 
 // Device-side batch descriptor (one per admitted batch).
@@ -59,6 +60,10 @@ struct ExecArgs {
     unsigned long long budget_ns;  // wall-clock bound of one launch
     unsigned long long *counters;  // [0] committed [1] gave up [2] aborts
     int *err;
+    // early validation (null when off): the watcher's stop flag, segments
+    // the ordered phase finished, and its segment count + 1 (0 = not known yet)
+    const unsigned int *stop;
+    unsigned int *segs_done, *segs_total;
     uint32_t cache_log2_sets;
     uint64_t key_base, val_base, lru_base, ver_base;
 };
@@ -191,6 +196,10 @@ __device__ __forceinline__ void rs_mark(uint32_t *rs, uint32_t *filter, uint64_t
     }
 }
 cudaError_t validate_setup();
+cudaError_t launch_watch(const hetm_log_entry *log, uint64_t n, const uint32_t *rs, uint32_t gshift,
+                         uint64_t n_words, unsigned int *stop, const unsigned int *segs_done,
+                         const unsigned int *segs_total, unsigned long long budget_ns, int blocks,
+                         cudaStream_t s);
 cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
                             uint64_t n_words, uint32_t *flags, unsigned long long *count,
                             uint32_t *ts, int *err, const uint32_t *filter, int blocks,

@@ -662,16 +662,33 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         for (int k = 0; k < 4; ++k) sm.ext[t][k] = 0ull;
     }
     if (t == 0) sm.abort = 0;
+    if (t == 0 && blockIdx.x == 0 && a.segs_total) st_rlx32((int32_t *)a.segs_total, (int32_t)(n_seg + 1));
     __syncthreads();
     for (;;) {
         if (t == 0) {
-            sm.seg = sm.abort ? 0xFFFFFFFFu : (uint32_t)atomicAdd(a.next, 1ull);
+            // sm.abort: 1 = the time budget ran out, 2 = early validation
+            // found a conflict; either way this CTA takes no new segment
+            if (!sm.abort && a.stop && ld_rlx32((const int32_t *)a.stop)) sm.abort = 2;
+            sm.seg = sm.abort == 1 ? 0xFFFFFFFFu : (uint32_t)atomicAdd(a.next, 1ull);
             sm.n_list = 0;
         }
         __syncthreads();
         const uint32_t g = sm.seg;
         if (g >= n_seg) break;
         const unsigned long long tag = (unsigned long long)(g + 1) << 32;
+        if (sm.abort == 2) {
+            // stopped by early validation: the rest of the phase only reports
+            // its transactions as not run
+            const uint32_t r = g * SEG + t;
+            if (!poller && r < n_ord) {
+                const OrdRec &q = o.rec[r];
+                const DevBatch &d = a.batches[q.meta >> 16];
+                if (d.status) d.status[q.li] = kNotRun;
+            }
+            __syncthreads();
+            if (t == 0 && a.segs_done) atomicAdd(a.segs_done, 1u);
+            continue;
+        }
 
         if (poller) {
             // ---------------- poll warp: external inputs still pending
@@ -680,6 +697,10 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             uint32_t passes = 0;
             while (n) {
                 if (*(volatile int *)&sm.abort) break;
+                if (a.stop && ld_rlx32((const int32_t *)a.stop)) {
+                    if (lane == 0) atomicCAS(&sm.abort, 0, 2);
+                    break;
+                }
                 if ((++passes & 15u) == 0 &&
                     __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns)
                     break;  // the executors see the budget run out themselves
@@ -938,15 +959,22 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             ++n_commit;
         }
         if (timed_out && !finished) {
-            if (o_status) o_status[rc.li] = kGaveUp;
-            ++n_gaveup;
-            set_err(a.err, kErrTimeout);
-            sm.abort = 1;
-            // release local successors so that they end too
+            if (*(volatile int *)&sm.abort == 2) {
+                // stopped by early validation: the round is lost to the CPU,
+                // this transaction never runs (its successors stop too)
+                if (o_status) o_status[rc.li] = kNotRun;
+            } else {
+                if (o_status) o_status[rc.li] = kGaveUp;
+                ++n_gaveup;
+                set_err(a.err, kErrTimeout);
+                sm.abort = 1;
+                // release local successors so that they end too
 #pragma unroll
-            for (int k = 0; k < 4; ++k) *(volatile unsigned long long *)&sm.pack[t][k] = tag;
+                for (int k = 0; k < 4; ++k) *(volatile unsigned long long *)&sm.pack[t][k] = tag;
+            }
         }
         __syncthreads();  // end of segment
+        if (t == 0 && a.segs_done) atomicAdd(a.segs_done, 1u);
     }
     if (poller) return;
 #pragma unroll

@@ -198,6 +198,48 @@ __global__ void __launch_bounds__(kValThreads) k_validate_direct(const hetm_log_
     validate_body<false>(log, n, rs, gshift, n_words, flags, count, nullptr, err, flt, stage);
 }
 
+// Early validation (Sec. IV-D): while the ordered executor runs, the round's
+// CPU log (already on the device) is validated again and again against
+// RS_bmp, whose bits the executor sets as transactions commit.  A hit means
+// the round will conflict whatever else commits, and under GPU-loses its
+// whole batch is rolled back: the watcher raises *stop and the executor
+// takes no new segment and runs no further transaction.  The final
+// validation still checks the whole log against the whole RS_bmp; the
+// watcher only saves the time of work that would be discarded.  It reads
+// RS_bmp through L2 (the executor's atomicOr lands there); a bit it misses
+// is caught by the final validation.  Every CTA leaves when the executor has
+// finished all its segments (*segs_done + 1 >= *segs_total), on a hit, or
+// after budget_ns.
+__global__ void __launch_bounds__(128) k_watch(const hetm_log_entry *__restrict__ log, uint64_t n,
+                                               const uint32_t *rs, uint32_t gshift, uint64_t n_words,
+                                               unsigned int *stop, const unsigned int *segs_done,
+                                               const unsigned int *segs_total,
+                                               unsigned long long budget_ns) {
+    __shared__ int s_quit;
+    const unsigned long long t0 = globaltimer_ns();
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint32_t scan = 0;; ++scan) {
+        bool hit = false;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n && !hit; i += stride) {
+            const uint32_t a = __ldg(&log[i].addr);
+            if (a < n_words) {
+                const uint32_t g = a >> gshift;
+                hit = (__ldcg(rs + (g >> 5)) >> (g & 31)) & 1u;
+            }
+        }
+        if (hit) atomicExch(stop, 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned int tot = *(volatile const unsigned int *)segs_total;
+            const unsigned int done = *(volatile const unsigned int *)segs_done;
+            s_quit = *(volatile unsigned int *)stop != 0 || (tot != 0 && done + 1 >= tot) ||
+                     globaltimer_ns() - t0 > budget_ns;
+        }
+        __syncthreads();
+        if (s_quit) return;
+    }
+}
+
 // Apply, second pass (Sec. IV-C): after TS holds the newest timestamp of
 // every logged word, exactly the tuple carrying it writes its value into
 // STMR^W and into the shadow STMR^S (Sec. IV-D: the shadow plus the CPU log
@@ -361,6 +403,14 @@ cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gsh
     else
         k_validate_round<false><<<blocks, kValThreads, smem, s>>>(rp, rs, gshift, n_words, flags, count,
                                                                   ts, err, filter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_watch(const hetm_log_entry *log, uint64_t n, const uint32_t *rs, uint32_t gshift,
+                         uint64_t n_words, unsigned int *stop, const unsigned int *segs_done,
+                         const unsigned int *segs_total, unsigned long long budget_ns, int blocks,
+                         cudaStream_t s) {
+    k_watch<<<blocks, 128, 0, s>>>(log, n, rs, gshift, n_words, stop, segs_done, segs_total, budget_ns);
     return cudaGetLastError();
 }
 

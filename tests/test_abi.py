@@ -83,3 +83,11 @@ def test_random_access_probe_rejects_bad_arguments_without_gpu():
     assert h.lib().hetm_random_access_rate(10, 100, ctypes.byref(r), None) == h.HETM_EINVAL
     assert h.lib().hetm_random_access_rate(24, 0, ctypes.byref(r), None) == h.HETM_EINVAL
     assert h.lib().hetm_random_access_rate(24, 100, None, None) == h.HETM_EINVAL
+
+
+def test_early_validation_fields_keep_layouts():
+    import paper_1905_00661_b300 as h
+    cfg = h.hetm_config_default()
+    assert cfg.early_validate == 0
+    assert ctypes.sizeof(h.hetm_config) == 128 and ctypes.sizeof(h.hetm_round_stats) == 88
+    assert h.hetm_round_stats.stopped_early.offset == 84
