@@ -330,6 +330,55 @@ def bench_round_at_scale(torch, h, v, reps=5):
     return out
 
 
+def bench_contention(torch, h, inputs, tuned, probs=(0.0, 0.25, 0.5, 0.75, 1.0), rounds=8):
+    """Throughput against the inter-device conflict probability (Sec. V-B's
+    contention study): in a given share of the rounds one CPU write, at a random
+    place of the log, goes to a word the GPU batch reads.  Commits count only in
+    rounds that validate clean; with early validation a conflicting round stops
+    executing as soon as the watcher sees the hit."""
+    init, batches, logs = inputs
+    rng = np.random.default_rng(SEED + 77)
+    out = {"p": list(probs), "rounds": rounds, "early": [], "no_early": [],
+           "early_round_ms": [], "no_early_round_ms": [], "stopped": []}
+    n_cf = {p: int(round(p * rounds)) for p in probs}
+    plans = {p: set(rng.choice(rounds, n_cf[p], replace=False).tolist()) for p in probs}
+    picks = [(int(rng.integers(N_TX)), int(rng.integers(N_LOG))) for _ in range(rounds)]
+    dev_tx = torch.from_numpy(batches[0].view(np.uint8)).cuda()
+    o = torch.empty(N_TX, dtype=torch.int64, device="cuda")
+    st_ = torch.empty(N_TX, dtype=torch.uint8, device="cuda")
+    res = torch.empty(N_TX, dtype=torch.int32, device="cuda")
+    cfg = dict({"cpu_threads": 1, "log_capacity": 1 << 12}, **tuned["config"])
+    for early in (1, 0):
+        with h.Context(1 << LOG2W, tuned["granule_bytes"], dict(cfg, early_validate=early)) as ctx:
+            ctx.load(init)
+            warm = torch.from_numpy(log_for_round(logs, 0).view(np.uint8)).cuda()
+            ctx.submit_batch(h.HETM_WL_RMW, dev_tx, o, st_, res, n_tx=N_TX)
+            ctx.log_attach(warm, N_LOG)
+            ctx.round(stats=True)
+            for pi, p in enumerate(probs):
+                clean, total_ms, stopped = 0, 0.0, 0
+                for r in range(rounds):
+                    lg = log_for_round(logs, 1 + pi * rounds + r)
+                    if r in plans[p]:
+                        j, pos = picks[r]
+                        lg["addr"][pos] = batches[0]["addr"][j][0]
+                    dlog = torch.from_numpy(lg.view(np.uint8)).cuda()
+                    ctx.submit_batch(h.HETM_WL_RMW, dev_tx, o, st_, res, n_tx=N_TX,
+                                     txid_base=(r * N_TX) & 0xFFFFFFFF)
+                    ctx.log_attach(dlog, N_LOG)
+                    st = ctx.round(stats=True)
+                    assert st["rc"] == h.HETM_OK and bool(st["conflict"]) == (r in plans[p])
+                    total_ms += st["ms_total"]
+                    clean += 0 if st["conflict"] else st["committed"]
+                    stopped += st["stopped_early"]
+                key = "early" if early else "no_early"
+                out[key].append(clean / (total_ms * 1e-3))
+                out[key + "_round_ms"].append(total_ms / rounds)
+                if early:
+                    out["stopped"].append(stopped)
+    return out
+
+
 def critical_path(tx):
     """Longest chain of conflicting update transactions in launch order (host, from the inputs)."""
     last, best = {}, 0
@@ -615,6 +664,7 @@ def main():
     chain = [critical_path(b) for b in inputs[1]]
     handoff_g, handoff_s = h.handoff_latency(20000)
     ra = h.random_access_rate(LOG2W, 1 << 28)
+    contention = bench_contention(torch, h, inputs, res["tuned"])
     w1 = [bench_w1_uniform(torch, h, inputs[0], f) for f in (0.1, 1.0)]
     for x in w1:
         x["random_roofline"] = random_bound({"reads": x.pop("word_reads"),
@@ -672,6 +722,7 @@ def main():
                        "writes": 4 * float(np.mean([int(b["flags"].sum()) for b in inputs[1]]))},
                       ra, exec_ms)},
         "random_access_per_s": {"read": ra[0], "write": ra[1], "array_words": 1 << LOG2W},
+        "contention": contention,
         "w1_uniform": w1,
         "cache": cache,
         "validation": {"kernel": "k_validate_direct", "ms": val["ms"], "gbs": val["gbs"],
