@@ -113,7 +113,7 @@ class Clocks:
 # ---------------------------------------------------------------------------
 def make_inputs(n_pool=2):
     """GPU batches Zipf(0.99) over the lower half of the STMR, CPU logs Zipf(0.99)
-    over the upper half: the two devices' partitions of Sec. V-A, so rounds
+    over the upper half: the two devices' partitions of Sec. V-B, so rounds
     validate clean and the GPU's commits survive."""
     init = wl.init_stmr(SEED, 1 << LOG2W)
     batches = [wl.rmw_batch(seed=SEED, batch=b, n_tx=N_TX, log2_words=LOG2W - 1)
@@ -331,7 +331,7 @@ def bench_round_at_scale(torch, h, v, reps=5):
 
 
 def bench_contention(torch, h, inputs, tuned, probs=(0.0, 0.25, 0.5, 0.75, 1.0), rounds=8):
-    """Throughput against the inter-device conflict probability (Sec. V-B's
+    """Throughput against the inter-device conflict probability (Sec. V-C's
     contention study): in a given share of the rounds one CPU write, at a random
     place of the log, goes to a word the GPU batch reads.  Commits count only in
     rounds that validate clean; with early validation a conflicting round stops

@@ -147,7 +147,23 @@ typedef struct hetm_config {
     void *(*dev_alloc)(size_t bytes, void *user);
     void (*dev_free)(void *ptr, void *user);
     void *alloc_user;
+    /* Inter-device conflict resolution (Sec. IV-E).  HETM_POLICY_GPU_LOSES
+     * (the paper's prototype): the CPU log is always applied and a conflict
+     * rolls the GPU batch back.  HETM_POLICY_CPU_LOSES: the CPU log is applied
+     * only after the whole validation came back clean; on a conflict the GPU
+     * state stands, the CPU log is discarded, and the host re-aligns its
+     * replica from its shadow and the GPU-dirty chunks (hetm_read_dirty). */
+    uint32_t conflict_policy;
+    /* GPU_LOSES only: after this many consecutive rounds that rolled the GPU
+     * back, the next execution phase admits only read-only CPU transactions
+     * (Sec. IV-E's anti-starvation rule; hetm_cpu_updates_allowed reports it
+     * and hetm_cpu_log_write refuses writes), so that round validates clean.
+     * 0 = off (default). */
+    uint32_t starve_limit;
 } hetm_config;
+
+#define HETM_POLICY_GPU_LOSES 0
+#define HETM_POLICY_CPU_LOSES 1
 
 /* Fill *cfg with the defaults listed above. */
 HETM_API int hetm_config_default(hetm_config *cfg);
@@ -311,7 +327,14 @@ typedef struct hetm_round_stats {
     float ms_exec, ms_validate, ms_apply, ms_merge, ms_total;
     uint32_t n_kernels;      /* kernel launches this round (graph kernel nodes) */
     uint32_t stopped_early;  /* 1: early validation stopped the execution phase */
+    uint32_t outcome;        /* HETM_OUTCOME_*: who won the round            */
+    uint32_t cpu_read_only_next; /* 1: anti-starvation -- the next execution
+                                    phase admits only read-only CPU transactions */
 } hetm_round_stats;
+
+#define HETM_OUTCOME_CLEAN 0          /* no conflict: both devices' commits stand   */
+#define HETM_OUTCOME_GPU_ROLLED_BACK 1 /* conflict, GPU loses: its batch is undone  */
+#define HETM_OUTCOME_CPU_DISCARDED 2  /* conflict, CPU loses: its log is discarded */
 
 /* One whole round: run the queued batches (persistent executor), ship the
  * CPU logs, validate, apply, merge, clear.  The device part is a CUDA graph
@@ -322,6 +345,21 @@ HETM_API int hetm_round(hetm_ctx *ctx, hetm_round_stats *stats);
 /* Wait for the round last launched by hetm_round(ctx, NULL) and fill *stats
  * (may be NULL).  Returns the round's status like hetm_round. */
 HETM_API int hetm_round_wait(hetm_ctx *ctx, hetm_round_stats *stats);
+
+/* Host side of the merge (Sec. IV-C merge phase, Sec. IV-E): copy into the
+ * host replica `host_stmr` (stmr_words int32, host memory) every WS_bmp
+ * chunk of the last completed round whose GPU writes survived it (a clean
+ * round, or a conflict the CPU lost), from STMR^S, contiguous dirty chunks
+ * in one copy.  After a round the GPU lost nothing is copied (the host
+ * replica already holds the round's outcome).  Under CPU_LOSES the caller
+ * first restores the words its discarded log wrote from its own shadow.
+ * *n_chunks / *n_bytes (may be NULL) get what was copied.  Synchronous. */
+HETM_API int hetm_read_dirty(hetm_ctx *ctx, int32_t *host_stmr, uint64_t *n_chunks, uint64_t *n_bytes);
+
+/* 1 when CPU update transactions may run in the current execution phase; 0
+ * while the anti-starvation rule holds the CPU to read-only transactions
+ * (starve_limit). */
+HETM_API int hetm_cpu_updates_allowed(hetm_ctx *ctx);
 
 /* ---------------------------------------------------------- serving (A7) */
 /* A serving loop over one context: client threads submit transaction

@@ -12,6 +12,8 @@ what a round must produce, from the definitions in the paper
                     than the stored timestamp (Sec. IV-C, array TS);
 * ``final_state``-- (conflict ? start : replayed) overlaid with the CPU image
                     (Sec. IV-C Merge Phase, Sec. IV-D rollback);
+* ``final_state_cpu_loses`` -- the CPU-loses policy (Sec. IV-E): the CPU
+                    image only after a clean validation, else the replay;
 * ``round_*``    -- the above composed for one round.
 
 Pins: every function is checked by ``tests/test_oracle.py`` against
@@ -179,10 +181,24 @@ class RoundResult:
         self.__dict__.update(kw)
 
 
-def round_from_replay(start, replayed, R, log, granule_bytes, ts_state):
+def final_state_cpu_loses(replayed, conflict, log, ts_state):
+    """Final STMR under the CPU-loses policy (Sec. IV-E): the CPU write-sets
+    are applied only when the whole validation found no conflict.  On a
+    conflict the apply is skipped, so the GPU's replayed state stands and
+    ``ts_state`` is left as it was; without one the round ends as under
+    GPU-loses (the replay overlaid with the newest-timestamp CPU image)."""
+    if conflict:
+        return replayed.copy(), 0
+    return final_state(replayed, replayed, False, log, ts_state)
+
+
+def round_from_replay(start, replayed, R, log, granule_bytes, ts_state, cpu_loses=False):
     """Validation + final state, given the GPU's replayed state and read granules R."""
     flags, n_conf = conflicts(log, R, granule_bytes)
-    final, ties = final_state(start, replayed, n_conf > 0, log, ts_state)
+    if cpu_loses:
+        final, ties = final_state_cpu_loses(replayed, n_conf > 0, log, ts_state)
+    else:
+        final, ties = final_state(start, replayed, n_conf > 0, log, ts_state)
     return RoundResult(flags=flags, n_conflicts=n_conf, conflict=n_conf > 0, final=final, ties=ties)
 
 

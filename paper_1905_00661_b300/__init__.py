@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libhetm.so")
 HETM_OK, HETM_EINVAL, HETM_ENOMEM, HETM_ECAPACITY = 0, -1, -2, -3
 HETM_ETIMEOUT, HETM_ECUDA, HETM_EBUSY, HETM_EDEVICE = -4, -5, -6, -7
 HETM_WL_BANK, HETM_WL_RMW, HETM_WL_CACHE = 1, 2, 3
+HETM_POLICY_GPU_LOSES, HETM_POLICY_CPU_LOSES = 0, 1
+HETM_OUTCOME_CLEAN, HETM_OUTCOME_GPU_ROLLED_BACK, HETM_OUTCOME_CPU_DISCARDED = 0, 1, 2
 HETM_EXEC_ORDERED, HETM_EXEC_OPTIMISTIC = 0, 1
 STMR_W, STMR_S, TS, RS_BMP, WS_BMP = 0, 1, 2, 3, 4
 
@@ -42,7 +44,7 @@ class hetm_config(ctypes.Structure):
                 ("cache_key_base", _u64), ("cache_val_base", _u64), ("cache_lru_base", _u64),
                 ("cache_ver_base", _u64), ("exec_mode", _u32), ("early_validate", _u32),
                 ("max_round_tx", _u64), ("dev_alloc", _ALLOC), ("dev_free", _FREE),
-                ("alloc_user", _vp)]
+                ("alloc_user", _vp), ("conflict_policy", _u32), ("starve_limit", _u32)]
 
 
 class hetm_batch(ctypes.Structure):
@@ -55,7 +57,8 @@ class hetm_round_stats(ctypes.Structure):
                 ("committed", _u64), ("gave_up", _u64), ("aborts", _u64), ("dirty_chunks", _u64),
                 ("n_batches", _u32), ("ms_exec", ctypes.c_float), ("ms_validate", ctypes.c_float),
                 ("ms_apply", ctypes.c_float), ("ms_merge", ctypes.c_float),
-                ("ms_total", ctypes.c_float), ("n_kernels", _u32), ("stopped_early", _u32)]
+                ("ms_total", ctypes.c_float), ("n_kernels", _u32), ("stopped_early", _u32),
+                ("outcome", _u32), ("cpu_read_only_next", _u32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,7 +73,8 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_round_wait", "hetm_server_config_default", "hetm_server_create",
            "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
            "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune",
-           "hetm_handoff_latency", "hetm_random_access_rate")
+           "hetm_handoff_latency", "hetm_random_access_rate", "hetm_read_dirty",
+           "hetm_cpu_updates_allowed")
 
 
 class hetm_tune_space(ctypes.Structure):
@@ -149,6 +153,8 @@ def _declare(L):
         "hetm_tune_space_default": (_int, [P(hetm_tune_space)]),
         "hetm_handoff_latency": (_int, [_u32, P(ctypes.c_double), P(ctypes.c_double)]),
         "hetm_random_access_rate": (_int, [_u32, _u64, P(ctypes.c_double), P(ctypes.c_double)]),
+        "hetm_read_dirty": (_int, [_vp, _vp, P(_u64), P(_u64)]),
+        "hetm_cpu_updates_allowed": (_int, [_vp]),
         "hetm_autotune": (_int, [_u64, _vp, P(hetm_batch), _u32, _vp, _u64, P(hetm_config),
                                  P(hetm_tune_space), P(hetm_config), P(_u32), P(hetm_tune_trial),
                                  _u32, P(_u32)]),
@@ -442,6 +448,19 @@ class Context:
         _ck(_lib.hetm_validate_only(self.h, _ptr(dev_log), n, _ptr(flags), _ptr(count)),
             "hetm_validate_only")
         self._leave()
+
+    def read_dirty(self, host_stmr: np.ndarray):
+        """Copy the last round's surviving GPU-dirty chunks into the host replica
+        (int32 numpy array of stmr_words); returns (chunks, bytes) copied."""
+        assert host_stmr.dtype == np.int32 and host_stmr.size == self.n_words
+        assert host_stmr.flags["C_CONTIGUOUS"]
+        c, b = _u64(), _u64()
+        _ck(_lib.hetm_read_dirty(self.h, host_stmr.ctypes.data, ctypes.byref(c), ctypes.byref(b)),
+            "hetm_read_dirty")
+        return c.value, b.value
+
+    def cpu_updates_allowed(self) -> bool:
+        return bool(_lib.hetm_cpu_updates_allowed(self.h))
 
     def merge(self, conflict=-1):
         self._enter()

@@ -116,6 +116,13 @@ struct hetm_ctx {
     cudaGraphExec_t g_exec = nullptr, g_sync = nullptr;
     uint32_t n_kern[2] = {0, 0};  // kernel nodes of g_exec / g_sync
     cudaEvent_t ev[7] = {};  // round timing: 0/6 around the executor, 1..4 in the sync graph, 5 end
+    // conflict policy: WS_bmp of the last round (pinned host copy, for
+    // hetm_read_dirty), whether that round's GPU writes survived, and the
+    // anti-starvation state
+    uint32_t *ws_host = nullptr;
+    bool last_gpu_survived = false;
+    uint32_t gpu_losses = 0;
+    std::atomic<bool> cpu_read_only{false};
     // early validation: watcher stream, "stop flag reset" node of g_exec, watcher done
     bool early = false;
     cudaStream_t watch = nullptr;
@@ -339,18 +346,35 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
     return HETM_OK;
 }
 
+// Validation + apply as the conflict policy wants them: GPU-loses fuses the
+// TS max into validation and applies unconditionally; CPU-loses validates
+// first and applies only when no tuple hit (both passes read the count).
+int enqueue_validate_apply(hetm_ctx *c, uint32_t *flags, cudaEvent_t *e) {
+    const bool cpu_loses = c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES;
+    CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, flags, &c->scr->conflicts,
+                       cpu_loses ? nullptr : c->TS, &c->scr->err, c->filter, c->n_sm, c->stream));
+    if (e) CK(cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
+    if (cpu_loses)
+        CK(launch_ts_max_if_clean(c->d_round, c->TS, c->n_words, &c->scr->conflicts, c->stream_blocks,
+                                  c->stream));
+    CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream,
+                    cpu_loses ? &c->scr->conflicts : nullptr));
+    return HETM_OK;
+}
+
 // validate (+ TS max) -> apply -> merge -> clear; events e[0..3] between
 // phases when non-null.
 int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e) {
     CK(cudaMemsetAsync(&c->scr->conflicts, 0, 2 * sizeof(unsigned long long), c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[0], c->stream, cudaEventRecordExternal));
-    CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, flags, &c->scr->conflicts, c->TS,
-                       &c->scr->err, c->filter, c->n_sm, c->stream));
-    if (e) CK(cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
-    CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream));
+    int rc = enqueue_validate_apply(c, flags, e);
+    if (rc != HETM_OK) return rc;
     if (e) CK(cudaEventRecordWithFlags(e[2], c->stream, cudaEventRecordExternal));
+    // CPU-loses: the GPU's writes stand whatever validation found (W -> S)
+    if (c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES) force = 0;
     CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, force,
                     &c->scr->dirty, c->stream_blocks, c->stream));
+    CK(cudaMemcpyAsync(c->ws_host, c->ws, c->ws_words * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
     CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
@@ -460,6 +484,7 @@ void hetm_destroy(hetm_ctx *c) {
         for (auto *b : L->buf)
             if (b) cudaFreeHost(b);
     if (c->out) cudaFreeHost(c->out);
+    if (c->ws_host) cudaFreeHost(c->ws_host);
     for (void *p : c->dev_allocs) {
         if (c->cfg.dev_free) c->cfg.dev_free(p, c->cfg.alloc_user);
         else cudaFree(p);
@@ -489,6 +514,7 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         return HETM_EINVAL;
     if (d.cache_log2_sets > 28) return HETM_EINVAL;
     if (d.exec_mode > HETM_EXEC_OPTIMISTIC) return HETM_EINVAL;
+    if (d.conflict_policy > HETM_POLICY_CPU_LOSES) return HETM_EINVAL;
     if (d.exec_mode == HETM_EXEC_ORDERED && (d.max_round_tx == 0 || d.max_round_tx > (1ull << 28)))
         return HETM_EINVAL;
 
@@ -563,7 +589,8 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         if (cudaEventCreateWithFlags(&s.used, cudaEventDisableTiming) != cudaSuccess)
             return fail(HETM_ECUDA);
     }
-    if (!host_alloc_t(&c->out, 1)) return fail(HETM_ENOMEM);
+    if (!host_alloc_t(&c->out, 1) || !host_alloc_t(&c->ws_host, c->ws_words)) return fail(HETM_ENOMEM);
+    std::memset(c->ws_host, 0, c->ws_words * 4);
     std::memset(c->out, 0, sizeof(RoundOut));
     for (int i = 0; i < 2; ++i) {
         if (cudaEventCreateWithFlags(&c->dlog_free[i], cudaEventDisableTiming) != cudaSuccess ||
@@ -734,6 +761,7 @@ int hetm_gpu_mark(hetm_ctx *c, const uint32_t *addr, const int32_t *vals, uint64
 
 int hetm_cpu_log_write(hetm_ctx *c, uint32_t thread, const hetm_log_entry *e, uint32_t n) {
     if (!c || thread >= c->tlogs.size() || (n && !e)) return HETM_EINVAL;
+    if (n && c->cpu_read_only.load()) return HETM_EBUSY;  // anti-starvation round
     ThreadLog &L = *c->tlogs[thread];
     std::lock_guard<std::mutex> g(L.mu);
     if (!L.buf[L.cur]) {
@@ -774,9 +802,8 @@ int hetm_validate(hetm_ctx *c, uint64_t *n_conflicts, uint32_t *dev_flag_bits) {
     if (rc != HETM_OK) return rc;
     CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
     CK(cudaMemsetAsync(&c->scr->conflicts, 0, sizeof(unsigned long long), c->stream));
-    CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, dev_flag_bits, &c->scr->conflicts,
-                       c->TS, &c->scr->err, c->filter, c->n_sm, c->stream));
-    CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream));
+    rc = enqueue_validate_apply(c, dev_flag_bits, nullptr);
+    if (rc != HETM_OK) return rc;
     CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
     if (n_conflicts) {
         unsigned long long h = 0;
@@ -863,6 +890,37 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
     return hetm_round_wait(c, stats);
 }
 
+int hetm_read_dirty(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_bytes) {
+    if (!c || !host) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    uint64_t chunks = 0, bytes = 0;
+    if (c->last_gpu_survived) {
+        const uint64_t wpc = 1ull << c->cshift;
+        const uint64_t n_chunk = (c->n_words + wpc - 1) / wpc;
+        uint64_t ch = 0;
+        while (ch < n_chunk) {
+            if (!((c->ws_host[ch >> 5] >> (ch & 31)) & 1u)) {
+                ++ch;
+                continue;
+            }
+            uint64_t end = ch + 1;  // coalesce a run of dirty chunks into one copy
+            while (end < n_chunk && ((c->ws_host[end >> 5] >> (end & 31)) & 1u)) ++end;
+            const uint64_t w0 = ch * wpc, w1 = std::min<uint64_t>(end * wpc, c->n_words);
+            CK(cudaMemcpyAsync(host + w0, c->S + w0, (w1 - w0) * 4, cudaMemcpyDeviceToHost, c->stream));
+            chunks += end - ch;
+            bytes += (w1 - w0) * 4;
+            ch = end;
+        }
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (n_chunks) *n_chunks = chunks;
+    if (n_bytes) *n_bytes = bytes;
+    return HETM_OK;
+}
+
+int hetm_cpu_updates_allowed(hetm_ctx *c) { return c && !c->cpu_read_only.load() ? 1 : 0; }
+
 int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     if (!c) return HETM_EINVAL;
     CK(cudaEventSynchronize(c->ev[5]));
@@ -888,6 +946,21 @@ int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     stats->n_batches = nb;
     stats->n_kernels = (nb ? c->n_kern[0] : 0) + c->n_kern[1] + (c->early && nb && n ? 1u : 0u);
     stats->stopped_early = c->early && nb && n ? c->out->stopped : 0u;
+    const bool cpu_loses = c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES;
+    stats->outcome = !stats->conflict ? HETM_OUTCOME_CLEAN
+                                      : (cpu_loses ? HETM_OUTCOME_CPU_DISCARDED : HETM_OUTCOME_GPU_ROLLED_BACK);
+    c->last_gpu_survived = stats->outcome != HETM_OUTCOME_GPU_ROLLED_BACK;
+    // anti-starvation (Sec. IV-E): a read-only CPU phase ends with its round;
+    // starve_limit consecutive GPU losses start one
+    c->cpu_read_only.store(false);
+    if (!cpu_loses && c->cfg.starve_limit && nb) {
+        c->gpu_losses = stats->outcome == HETM_OUTCOME_GPU_ROLLED_BACK ? c->gpu_losses + 1 : 0;
+        if (c->gpu_losses >= c->cfg.starve_limit) {
+            c->gpu_losses = 0;
+            c->cpu_read_only.store(true);
+            stats->cpu_read_only_next = 1;
+        }
+    }
     float ms = 0;
     if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[6]) == cudaSuccess) stats->ms_exec = ms;
     if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) stats->ms_validate = ms;

@@ -209,7 +209,10 @@ cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const 
                                    unsigned long long *count, int *err, const uint32_t *filter,
                                    int blocks, cudaStream_t s);
 cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int32_t *S,
-                         uint64_t n_words, int blocks, cudaStream_t s);
+                         uint64_t n_words, int blocks, cudaStream_t s,
+                         const unsigned long long *skip_if = nullptr);
+cudaError_t launch_ts_max_if_clean(const DevRound *rp, uint32_t *ts, uint64_t n_words,
+                                   const unsigned long long *conflicts, int blocks, cudaStream_t s);
 cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_t *S,
                          uint64_t n_words, const unsigned long long *conflicts, int force,
                          unsigned long long *dirty_count, int blocks, cudaStream_t s);

@@ -244,9 +244,28 @@ __global__ void __launch_bounds__(128) k_watch(const hetm_log_entry *__restrict_
 // every logged word, exactly the tuple carrying it writes its value into
 // STMR^W and into the shadow STMR^S (Sec. IV-D: the shadow plus the CPU log
 // is the CPU's state).  Out-of-range tuples were reported by validation.
+// CPU-loses policy (Sec. IV-E): the CPU log is applied only when the whole
+// validation came back clean, so the TS max runs as its own pass after
+// validation and, like the apply, does nothing once a conflict was counted.
+__global__ void __launch_bounds__(256) k_ts_max_if_clean(const DevRound *rp, uint32_t *ts,
+                                                         uint64_t n_words,
+                                                         const unsigned long long *conflicts) {
+    if (*(volatile const unsigned long long *)conflicts) return;
+    const hetm_log_entry *log = rp->log;
+    const uint64_t n = rp->n_log;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t a = __ldg(&log[i].addr);
+        if (a < n_words) ts_raise(ts, a, __ldg(&log[i].ts));
+    }
+}
+
+// skip_if (may be null): the round's conflict count; a nonzero count skips
+// the apply (CPU-loses policy).
 __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_t *__restrict__ ts,
                                                int32_t *__restrict__ W, int32_t *__restrict__ S,
-                                               uint64_t n_words) {
+                                               uint64_t n_words, const unsigned long long *skip_if) {
+    if (skip_if && *(volatile const unsigned long long *)skip_if) return;
     __shared__ uint4 s_stage[256 / 32 * kTileVec];
     const hetm_log_entry *log = rp->log;
     const uint64_t n = rp->n_log;
@@ -425,8 +444,15 @@ cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const 
 }
 
 cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int32_t *S,
-                         uint64_t n_words, int blocks, cudaStream_t s) {
-    k_apply<<<blocks, 256, 0, s>>>(rp, ts, W, S, n_words);
+                         uint64_t n_words, int blocks, cudaStream_t s,
+                         const unsigned long long *skip_if) {
+    k_apply<<<blocks, 256, 0, s>>>(rp, ts, W, S, n_words, skip_if);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ts_max_if_clean(const DevRound *rp, uint32_t *ts, uint64_t n_words,
+                                   const unsigned long long *conflicts, int blocks, cudaStream_t s) {
+    k_ts_max_if_clean<<<blocks, 256, 0, s>>>(rp, ts, n_words, conflicts);
     return cudaGetLastError();
 }
 

@@ -40,8 +40,8 @@ def test_record_layouts_match_workloads():
     import workloads as wl
     assert h.LOG_DTYPE == wl.LOG_DTYPE
     assert ctypes.sizeof(h.hetm_batch) == 48
-    assert ctypes.sizeof(h.hetm_config) == 128
-    assert ctypes.sizeof(h.hetm_round_stats) == 88
+    assert ctypes.sizeof(h.hetm_config) == 136
+    assert ctypes.sizeof(h.hetm_round_stats) == 96
 
 
 def test_init_rejects_bad_arguments_before_touching_the_device():
@@ -89,5 +89,36 @@ def test_early_validation_fields_keep_layouts():
     import paper_1905_00661_b300 as h
     cfg = h.hetm_config_default()
     assert cfg.early_validate == 0
-    assert ctypes.sizeof(h.hetm_config) == 128 and ctypes.sizeof(h.hetm_round_stats) == 88
+    assert cfg.conflict_policy == h.HETM_POLICY_GPU_LOSES and cfg.starve_limit == 0
     assert h.hetm_round_stats.stopped_early.offset == 84
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets that
+    gcc gives the same struct from include/hetm.h."""
+    import shutil
+    import subprocess
+    import paper_1905_00661_b300 as h
+    if not shutil.which("gcc"):
+        import pytest
+        pytest.skip("no gcc")
+    structs = [h.hetm_config, h.hetm_round_stats, h.hetm_batch, h.hetm_tune_space,
+               h.hetm_tune_trial, h.hetm_request, h.hetm_server_config, h.hetm_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hetm.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"

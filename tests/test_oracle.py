@@ -294,3 +294,38 @@ def test_validation_config_hits_exact_at_small_scale():
     v = wl.validation_round(seed=1, log2_words=18, n_log=1 << 15)
     flags, n = oracle.conflicts(v.log, v.read_granules, v.granule_bytes)
     assert n == v.n_hits_planted == round(0.02 * (1 << 15))
+
+
+def _log_rows(rows):
+    a = np.zeros(len(rows), wl.LOG_DTYPE)
+    for i, r in enumerate(rows):
+        a[i] = tuple(r)
+    return a
+
+
+def test_cpu_loses_policy_hand_enumerated():
+    """Sec. IV-E: under CPU-loses the CPU write-sets are applied only after a
+    clean validation.  Eight words 10..17; the GPU's replay wrote 99 into word 2
+    and read word 3 (G = 4 B: granules 2 and 3)."""
+    start = np.arange(10, 18, dtype=np.int32)
+    replayed = start.copy()
+    replayed[2] = 99
+    R = np.array([2, 3], np.uint32)
+    hit = _log_rows([(3, 50, 1), (6, 60, 2)])     # word 3 was read by the GPU
+    clean = _log_rows([(6, 60, 2)])
+    # conflict, GPU loses: start + CPU writes
+    g = oracle.round_from_replay(start, replayed, R, hit, 4, np.zeros(8, np.uint32))
+    assert g.conflict
+    np.testing.assert_array_equal(g.final, [10, 11, 12, 50, 14, 15, 60, 17])
+    # conflict, CPU loses: the GPU's state, no CPU write, TS untouched
+    ts = np.zeros(8, np.uint32)
+    c = oracle.round_from_replay(start, replayed, R, hit, 4, ts, cpu_loses=True)
+    assert c.conflict
+    np.testing.assert_array_equal(c.final, [10, 11, 99, 13, 14, 15, 16, 17])
+    assert not ts.any()
+    # no conflict: both policies give replay + CPU writes
+    for cpu_loses in (False, True):
+        r = oracle.round_from_replay(start, replayed, R, clean, 4, np.zeros(8, np.uint32),
+                                     cpu_loses=cpu_loses)
+        assert not r.conflict
+        np.testing.assert_array_equal(r.final, [10, 11, 99, 13, 14, 15, 60, 17])

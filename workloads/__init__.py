@@ -426,7 +426,7 @@ def cpu_write_log(seed: int, rnd: int, n: int, log2_words: int, q: float = 0.99,
     """Per-thread CPU logs of plain writes for one round; ts = ts_base + 1 .. ts_base + n.
 
     Zipf addresses fall in [offset, offset + 2^log2_words): with ``offset`` the
-    log covers another partition of the STMR than the GPU's (Sec. V-A splits
+    log covers another partition of the STMR than the GPU's (Sec. V-B splits
     the STMR in two halves, one per device)."""
     n_words = 1 << log2_words
     hi = n_words if hi is None else hi
