@@ -241,6 +241,8 @@ def bench_ours(args, rank, world, local_rank, inputs):
     vround = wl.validation_round(seed=1, log2_words=LOG2W, with_init=False)
     val = bench_validation(torch, h, vround)
     val["round"] = bench_round_at_scale(torch, h, vround)
+    if rank == 0:
+        val["cpu_mt"] = cpu_mt_sync(vround)
     del vround
     res = {"ms": ms, "committed": committed, "exec_ms": exec_ms, "exec_bytes": exec_bytes,
            "tuned": {"seconds": t_tune, "config": tuned["config"], "granule_bytes": granule,
@@ -377,6 +379,28 @@ def bench_contention(torch, h, inputs, tuned, probs=(0.0, 0.25, 0.5, 0.75, 1.0),
                 if early:
                     out["stopped"].append(stopped)
     return out
+
+
+def cpu_mt_sync(v):
+    """The timed multithreaded CPU baseline (std::thread, every host core) of
+    validation + apply on the same 16.8M-tuple log and 2^28-word STMR."""
+    import oracle
+    n = 1 << LOG2W
+    wpg = v.granule_bytes // 4
+    R = v.read_granules
+    rs = np.zeros((n // wpg + 31) // 32, np.uint32)
+    np.bitwise_or.at(rs, R // 32, (np.uint32(1) << (R % 32).astype(np.uint32)))
+    W = np.zeros(n, np.int32)
+    S = np.zeros(n, np.int32)
+    TS = np.zeros(n, np.uint32)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    hits = oracle.cpu_validate_apply_mt(v.log, rs, v.granule_bytes, W, S, TS, threads)
+    dt = time.perf_counter() - t0
+    n_log = len(v.log)
+    return {"kind": "multithreaded CPU baseline (validate + apply)", "threads": threads,
+            "ms": dt * 1e3, "gbs": (12 * n_log + n_log / 8) / dt / 1e9, "hits": hits,
+            "sample": f"the whole {n_log}-tuple log, 2^{LOG2W}-word STMR in host memory"}
 
 
 def critical_path(tx):
@@ -601,6 +625,16 @@ def run_case(name):
     raise SystemExit(f"unknown case {name}")
 
 
+def combine_ranks(torch, dist, device, ms, e2e_s, committed, e2e_commit):
+    """Whole-job figures of N replicas (one per GPU, no data-path collective):
+    the slowest rank's times and the commits of all ranks."""
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([committed, e2e_commit], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(c[0]), int(c[1])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -650,12 +684,8 @@ def main():
     ms, committed = res["ms"], res["committed"]
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms, res["e2e_s"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([committed, res["e2e_commit"]], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        ms, e2e_s = float(t[0]), float(t[1])
-        committed, e2e_commit = int(c[0]), int(c[1])
+        ms, e2e_s, committed, e2e_commit = combine_ranks(torch, dist, "cuda", ms, res["e2e_s"],
+                                                         committed, res["e2e_commit"])
     else:
         e2e_s, e2e_commit = res["e2e_s"], res["e2e_commit"]
     if rank != 0:
@@ -729,7 +759,7 @@ def main():
                        "frac": val["gbs"] / res["hbm"], "bytes": val["bytes"],
                        "hits": val["hits"], "hits_expected": val["hits_expected"],
                        "workload": "validation_2^28w_16Mlog_g64",
-                       "sync_phase": val["round"]},
+                       "sync_phase": val["round"], "cpu_mt": val.get("cpu_mt")},
         "e2e": {"value": e2e_commit / e2e_s, "unit": "tx/s",
                 "h2d_bytes_per_step": N_TX * 20 + N_LOG * 12,
                 "d2h_bytes_per_step": N_TX * (8 + 1 + 4)},

@@ -16,6 +16,11 @@ what a round must produce, from the definitions in the paper
                     image only after a clean validation, else the replay;
 * ``round_*``    -- the above composed for one round.
 
+``cpu_validate_apply_mt`` is not part of the oracle: it is the timed CPU
+baseline of the synchronization phase (``cpu_baseline.cpp``, std::thread),
+checked against the oracle in ``tests/test_oracle.py`` and timed by
+``bench.py``.
+
 Pins: every function is checked by ``tests/test_oracle.py`` against
 hand-enumerated rounds (``tests/golden/``), closed forms, invariants and
 brute force over serial orders.  No function here is "parity unpinned".
@@ -38,10 +43,18 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _c_u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
+_MT_SRC = os.path.join(_HERE, "cpu_baseline.cpp")
+_MT_LIB = os.path.join(_HERE, "libcpubase.so")
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (g++, no GPU needed)."""
+    """Compile the oracle into ``oracle/liboracle.so`` and the timed CPU
+    baseline into ``oracle/libcpubase.so`` (g++, no GPU needed)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", _LIB])
+    if force or not os.path.exists(_MT_LIB) or os.path.getmtime(_MT_LIB) < os.path.getmtime(_MT_SRC):
+        subprocess.check_call(["g++", "-O3", "-std=c++17", "-pthread", "-shared", "-fPIC", _MT_SRC,
+                               "-o", _MT_LIB])
     return _LIB
 
 
@@ -233,3 +246,27 @@ def round_planted(start, read_granules, plant_addr, plant_value, log, granule_by
     res = round_from_replay(start, replayed, R, log, granule_bytes, ts_state)
     res.replayed, res.R, res.ts_state = replayed, R, ts_state
     return res
+
+
+_mt = None
+
+
+def cpu_validate_apply_mt(log, rs_words, granule_bytes, W, S, TS, threads, flags=None):
+    """Timed CPU baseline: validation + apply of ``log`` against the RS_bmp
+    words ``rs_words`` on host W, S, TS (updated in place) with ``threads``
+    std::threads; returns the hit count."""
+    global _mt
+    if _mt is None:
+        build()
+        _mt = ctypes.CDLL(_MT_LIB)
+        vp = ctypes.c_void_p
+        _mt.hetm_cpu_validate_apply_mt.argtypes = [vp, ctypes.c_uint64, vp, ctypes.c_uint32,
+                                                   ctypes.c_uint64, vp, vp, vp, vp, ctypes.c_int]
+        _mt.hetm_cpu_validate_apply_mt.restype = ctypes.c_int64
+    rs = np.ascontiguousarray(rs_words, np.uint32)
+    gshift = int(np.log2(granule_bytes // 4))
+    n = _mt.hetm_cpu_validate_apply_mt(_p(log), len(log), _p(rs), gshift, W.size, _p(W), _p(S), _p(TS),
+                                       None if flags is None else _p(flags), int(threads))
+    if n < 0:
+        raise ValueError("log address out of range")
+    return int(n)

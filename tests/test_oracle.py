@@ -329,3 +329,29 @@ def test_cpu_loses_policy_hand_enumerated():
                                      cpu_loses=cpu_loses)
         assert not r.conflict
         np.testing.assert_array_equal(r.final, [10, 11, 99, 13, 14, 15, 60, 17])
+
+
+def test_cpu_baseline_mt_matches_oracle():
+    """The timed multithreaded CPU baseline computes what the oracle defines:
+    the same flags and hit count, and the same newest-timestamp apply."""
+    v = wl.validation_round(seed=3, log2_words=18, n_log=1 << 15)
+    n = 1 << 18
+    wpg = v.granule_bytes // 4
+    R = v.read_granules
+    rs = np.zeros((n // wpg + 31) // 32, np.uint32)
+    np.bitwise_or.at(rs, R // 32, (np.uint32(1) << (R % 32).astype(np.uint32)))
+    ref_flags, ref_n = oracle.conflicts(v.log, R, v.granule_bytes)
+    for threads in (1, 3, 8):
+        W = v.init.copy()
+        S = v.init.copy()
+        TS = np.zeros(n, np.uint32)
+        flags = np.zeros(len(v.log), np.uint8)
+        hits = oracle.cpu_validate_apply_mt(v.log, rs, v.granule_bytes, W, S, TS, threads, flags)
+        assert hits == ref_n == v.n_hits_planted
+        np.testing.assert_array_equal(flags, ref_flags)
+        want = v.init.copy()
+        ts = np.zeros(n, np.uint32)
+        assert oracle.cpu_image(want, ts, v.log) == 0
+        np.testing.assert_array_equal(W, want)
+        np.testing.assert_array_equal(S, want)
+        np.testing.assert_array_equal(TS, ts)
