@@ -576,11 +576,12 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
             !dev_alloc_t(c, &o.keys1, o.cap_acc) || !dev_alloc_t(c, &o.vals1, o.cap_acc) ||
             !dev_alloc_t(c, &o.hist, hist_n) || !dev_alloc_t(c, &o.runs, o.cap_acc) ||
             !dev_alloc_t(c, &o.rec, o.cap_tx) || !dev_alloc_t(c, &o.packed, o.cap_acc) ||
-            !dev_alloc_t(c, &o.n_acc, 4) ||
+            !dev_alloc_t(c, &o.n_acc, 4) || !dev_alloc_t(c, &o.cache_heads, o.cap_tx) ||
             !dev_alloc_t(c, &o.v0, 1))
             return fail(HETM_ENOMEM);
         o.n_ord = o.n_acc + 1;
         o.n_tx32 = o.n_acc + 2;
+        o.n_cache_runs = o.n_acc + 3;
     }
     for (auto &s : c->stage) {
         if (!host_alloc_t(&s.rounds, nb + 1) || !host_alloc_t(&s.batches, nb) ||

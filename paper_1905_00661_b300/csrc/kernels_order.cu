@@ -367,6 +367,7 @@ __global__ void __launch_bounds__(256) k_ord_count(OrderArgs o) {
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (tid == 0) {
         *o.n_tx32 = (uint32_t)total;
+        *o.n_cache_runs = 0;
         const unsigned long long v0 = *a.gv;
         *o.v0 = v0;
         *a.gv = v0 + total + 1;  // this launch owns versions v0+1 .. v0+total+1
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(256) k_ord_runs(OrderArgs o) {
         const bool writer = o.vals0[i] & 1u;
         o.runs[i] = ((head ? i : 0ull) << 32) | (writer ? i + 1 : 0ull);
         o.packed[i] = 0ull;
+        if (head && (o.vals0[i] & 2u)) o.cache_heads[atomicAdd(o.n_cache_runs, 1u)] = (uint32_t)i;
     }
 }
 
@@ -523,81 +525,85 @@ __device__ __forceinline__ void mark_range(const ExecArgs &a, uint64_t w0, uint3
             atomicOr(a.ws + (c >> 5), 1u << (c & 31));
 }
 
-__device__ __forceinline__ uint4 ld_volatile16(const int32_t *p) {
-    uint4 v;
-    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p)
-                 : "memory");
-    return v;
-}
 
-// One cache request on its set, which this thread holds (PUT) or shares (GET).
-__device__ void cache_request(const ExecArgs &a, const hetm_cache_req &r, uint32_t stamp,
-                              uint64_t &out) {
-    const uint32_t set = (uint32_t)(splitmix_fin(r.key) & ((1ull << a.cache_log2_sets) - 1));
-    const uint64_t kw = a.key_base + 16ull * set;
-    uint64_t keys[8];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint4 v = ld_volatile16(a.W + kw + 4 * q);
-        keys[2 * q] = ((uint64_t)v.y << 32) | v.x;
-        keys[2 * q + 1] = ((uint64_t)v.w << 32) | v.z;
-    }
+// Object cache (Sec. V-D).  A request touches only its own set, so the
+// requests of different sets never depend on each other and only each set's
+// own requests need the launch order.  The sorted access list holds them as
+// one run per set; one warp takes a run, keeps the set (8 keys, 8 values, 8
+// GPU stamps, version) in registers -- the same copy in every lane -- and
+// applies the run's requests in rank order, 32 staged at a time (each lane
+// loads one, then every lane applies them all in turn).  The changed words go
+// back once per run, and the read/write-set marks of all its requests are
+// applied once, spread over the lanes.  No hand-on between warps is needed.
+// (Word transactions of the same launch must not touch the cache regions.)
+struct CacheMarks {
+    uint32_t keys_read, lru_all_read, ver_write;
+    uint32_t val_read, val_write, key_write, lru_write;  // bit w: way w
+};
+
+// One request applied to the set copy; returns the request's output.
+__device__ __forceinline__ uint64_t cache_apply(uint64_t (&keys)[8], uint64_t (&vals)[8], uint32_t (&lru)[8],
+                                                uint32_t &ver, uint32_t &dirty_kv, uint32_t &dirty_lru,
+                                                uint64_t key, uint64_t value, uint32_t op, uint32_t stamp,
+                                                CacheMarks &mk) {
     int hit = -1, empty = -1;
 #pragma unroll
     for (int w = 7; w >= 0; --w) {
-        if (keys[w] == r.key) hit = w;
+        if (keys[w] == key) hit = w;
         if (keys[w] == 0) empty = w;
     }
-    mark_range(a, kw, 16, false);
-    if (r.op == 0) {
-        if (hit < 0) {
-            out = ~0ull;
-            return;
-        }
-        const uint64_t vw = a.val_base + 2ull * (8ull * set + hit);
-        const uint64_t lw = a.lru_base + 8ull * set + hit;
-        out = ld_rlx_u64(a.W + vw);
-        // GETs of a set run concurrently: their stamps grow with the serial
-        // order, so the max is the stamp of the last one
-        atomicMax(reinterpret_cast<unsigned int *>(a.W + lw), stamp);
-        mark_range(a, vw, 2, false);
-        mark_range(a, lw, 1, true);
-        return;
+    mk.keys_read = 1;
+    if (op == 0) {  // GET: a hit reads the value and stamps the way
+        if (hit < 0) return ~0ull;
+        uint64_t out = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+            if (w == hit) {
+                out = vals[w];
+                lru[w] = max(lru[w], stamp);
+            }
+        dirty_lru |= 1u << hit;
+        mk.val_read |= 1u << hit;
+        mk.lru_write |= 1u << hit;
+        return out;
     }
-    const uint64_t verw = a.ver_base + set;
-    uint32_t way;
+    // PUT: update in place, else the first empty way, else the least recently
+    // stamped way (lowest way on ties)
+    int way;
     if (hit >= 0) {
-        way = (uint32_t)hit;
+        way = hit;
     } else if (empty >= 0) {
-        way = (uint32_t)empty;
+        way = empty;
     } else {
-        const uint4 l0 = ld_volatile16(a.W + a.lru_base + 8ull * set);
-        const uint4 l1 = ld_volatile16(a.W + a.lru_base + 8ull * set + 4);
-        const uint32_t l[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
         way = 0;
-        uint32_t best = l[0];
+        uint32_t best = lru[0];
 #pragma unroll
         for (int w = 1; w < 8; ++w)
-            if (l[w] < best) {
-                best = l[w];
-                way = (uint32_t)w;
+            if (lru[w] < best) {
+                best = lru[w];
+                way = w;
             }
-        mark_range(a, a.lru_base + 8ull * set, 8, false);
+        mk.lru_all_read = 1;
     }
-    const uint64_t slot = 8ull * set + way;
-    if (hit < 0) {
-        st_rlx_u64w(a.W + a.key_base + 2 * slot, r.key);
-        mark_range(a, a.key_base + 2 * slot, 2, true);
-    }
-    st_rlx_u64w(a.W + a.val_base + 2 * slot, r.value);
-    st_rlx32(a.W + a.lru_base + slot, (int32_t)stamp);
-    st_rlx32(a.W + verw, ld_rlx32(a.W + verw) + 1);
-    mark_range(a, a.val_base + 2 * slot, 2, true);
-    mark_range(a, a.lru_base + slot, 1, true);
-    mark_range(a, verw, 1, true);
-    out = way;
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+        if (w == way) {
+            keys[w] = key;
+            vals[w] = value;
+            lru[w] = stamp;
+        }
+    if (hit < 0) mk.key_write |= 1u << way;
+    dirty_kv |= 1u << way;
+    dirty_lru |= 1u << way;
+    ++ver;
+    mk.val_write |= 1u << way;
+    mk.lru_write |= 1u << way;
+    mk.ver_write = 1;
+    return (uint64_t)way;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int l) {
+    return ((uint64_t)__shfl_sync(kFull, (uint32_t)(v >> 32), l) << 32) | __shfl_sync(kFull, (uint32_t)v, l);
 }
 
 // Ordered phase, CTA-segment executor.  A CTA takes segments of SEG
@@ -782,13 +788,11 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         uint64_t *o_order = nullptr;
         uint8_t *o_status = nullptr;
         void *o_out = nullptr;
-        const void *o_tx = nullptr;
         if (n) {
             const DevBatch &d = a.batches[rc.meta >> 16];
             o_order = d.order;
             o_status = d.status;
             o_out = d.out;
-            o_tx = d.tx;
         }
         // W1 update naming 4 distinct words (the common case): slot j = word j
         const bool rmw4 = wl == HETM_WL_RMW && n == 4 && ((rc.meta >> 8) & 0xFFu) == 0xE4u;
@@ -798,7 +802,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         uint32_t ext = 0, loc = 0;  // slots still waiting on an earlier segment / this segment
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (k >= (int)n) continue;
+            if (k >= (int)n || cache) continue;
             const uint32_t tf = rc.turn[k];
             if (!cache && (tf & kFLocal)) loc |= 1u << k;
             else if (cache || (tf & kTurnMask)) ext |= 1u << k;
@@ -842,7 +846,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         }
         __syncthreads();  // the pending list is complete: the poll warp starts
 
-        bool finished = n == 0;
+        bool finished = n == 0 || cache;  // cache requests run in k_cache_runs
         bool executed = false;
         bool timed_out = false;
         // Each slot still pending watches one shared word: its predecessor's
@@ -873,7 +877,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 pend &= got ? ~(1u << k) : ~0u;
             }
             const bool ready = !finished && pend == 0;
-            if (ready && !cache) {
+            if (ready) {
                 if (rmw4) {
                     sum = cur[0] + cur[1] + cur[2] + cur[3];
 #pragma unroll
@@ -910,17 +914,6 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                         st_rlx64(o.packed + rc.res[k],
                                  ((unsigned long long)((rc.turn[k] & kTurnMask) + 1) << 32) |
                                      (uint32_t)nv[k]);
-                finished = true;
-                executed = true;
-            } else if (ready) {  // cache request: holds or shares its set
-                const unsigned long long key = 2ull * (v0 + 1 + rc.u);
-                fence_gpu();  // acquire the set's previous holders' writes
-                const hetm_cache_req q = static_cast<const hetm_cache_req *>(o_tx)[rc.li];
-                uint64_t out = 0;
-                cache_request(a, q, (uint32_t)(key >> 1), out);
-                fence_gpu();  // release before handing the set on
-                atomicAdd(o.packed + rc.res[0], 1ull << 32);
-                if (o_out) static_cast<uint64_t *>(o_out)[rc.li] = out;
                 finished = true;
                 executed = true;
             }
@@ -988,6 +981,118 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
     }
 }
 
+// One warp per cache run (see cache_apply).  Early validation's stop flag
+// leaves runs not yet started as not run.
+__global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
+    const ExecArgs &a = o.e;
+    const uint32_t n_runs = *o.n_cache_runs;
+    if (n_runs == 0) return;
+    const uint32_t n_acc = *o.n_acc;
+    const unsigned long long v0 = *o.v0;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long n_commit = 0;
+    for (uint32_t ri = warp; ri < n_runs; ri += n_warps) {
+        const uint32_t head = o.cache_heads[ri];
+        const uint32_t res = o.keys0[head];  // the set's version word
+        const uint32_t set = res - (uint32_t)a.ver_base;
+        const bool stopped = a.stop && __shfl_sync(kFull, ld_rlx32((const int32_t *)a.stop), 0);
+        const uint64_t kw = a.key_base + 16ull * set, vb = a.val_base + 16ull * set;
+        const uint64_t lb = a.lru_base + 8ull * set;
+        uint64_t keys[8], vals[8];
+        uint32_t lru[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 k = *reinterpret_cast<const uint4 *>(a.W + kw + 4 * q);
+            const uint4 v = *reinterpret_cast<const uint4 *>(a.W + vb + 4 * q);
+            keys[2 * q] = ((uint64_t)k.y << 32) | k.x;
+            keys[2 * q + 1] = ((uint64_t)k.w << 32) | k.z;
+            vals[2 * q] = ((uint64_t)v.y << 32) | v.x;
+            vals[2 * q + 1] = ((uint64_t)v.w << 32) | v.z;
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const uint4 l = *reinterpret_cast<const uint4 *>(a.W + lb + 4 * q);
+            lru[4 * q] = l.x;
+            lru[4 * q + 1] = l.y;
+            lru[4 * q + 2] = l.z;
+            lru[4 * q + 3] = l.w;
+        }
+        uint32_t ver = (uint32_t)a.W[res], ver0 = ver, dirty_kv = 0, dirty_lru = 0;
+        CacheMarks mk{};
+        for (uint32_t base = head;; base += 32) {
+            const uint32_t j = base + lane;
+            const bool in = j < n_acc && o.keys0[j] == res;
+            const unsigned m = __ballot_sync(kFull, in);  // the run is contiguous: a prefix
+            uint64_t key = 0, value = 0;
+            uint32_t op = 0, li = 0, u = 0;
+            const DevBatch *d = nullptr;
+            if (in) {
+                const OrdRec &q = o.rec[o.vals0[j] >> 4];
+                li = q.li;
+                u = q.u;
+                d = a.batches + (q.meta >> 16);
+                const hetm_cache_req r = static_cast<const hetm_cache_req *>(d->tx)[li];
+                key = r.key;
+                value = r.value;
+                op = r.op & 1u;
+            }
+            const int cnt = __popc(m);
+            uint64_t my_out = 0;
+            if (!stopped) {
+                for (int l = 0; l < cnt; ++l) {
+                    const uint64_t k_ = shfl64(key, l), v_ = shfl64(value, l);
+                    const uint32_t op_ = __shfl_sync(kFull, op, l);
+                    const uint32_t stamp = (uint32_t)(v0 + 1 + __shfl_sync(kFull, u, l));
+                    const uint64_t out = cache_apply(keys, vals, lru, ver, dirty_kv, dirty_lru, k_, v_, op_,
+                                                     stamp, mk);
+                    if ((int)lane == l) my_out = out;
+                }
+            }
+            if (in) {
+                if (stopped) {
+                    if (d->status) d->status[li] = kNotRun;
+                } else {
+                    if (d->out) static_cast<uint64_t *>(d->out)[li] = my_out;
+                    if (d->order) d->order[li] = 2ull * (v0 + 1 + u);
+                    if (d->status) d->status[li] = kCommitted;
+                }
+            }
+            if (!stopped) n_commit += in ? 1u : 0u;
+            if (cnt < 32) break;
+        }
+        if (stopped) continue;
+        // write back what changed: lane w owns way w
+        if (lane < 8) {
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+                if ((int)lane == w) {
+                    if (dirty_kv & (1u << w)) {
+                        st_rlx_u64w(a.W + kw + 2 * w, keys[w]);
+                        st_rlx_u64w(a.W + vb + 2 * w, vals[w]);
+                    }
+                    if (dirty_lru & (1u << w)) st_rlx32(a.W + lb + w, (int32_t)lru[w]);
+                }
+        }
+        if (lane == 8 && ver != ver0) st_rlx32(a.W + res, (int32_t)ver);
+        // read/write-set marks of the whole run, one range per lane
+        if (lane == 9 && mk.keys_read) mark_range(a, kw, 16, false);
+        if (lane == 10 && mk.lru_all_read) mark_range(a, lb, 8, false);
+        if (lane == 11 && mk.ver_write) mark_range(a, res, 1, true);
+        if (lane >= 12 && lane < 20) {
+            const uint32_t w = lane - 12;
+            if (mk.key_write & (1u << w)) mark_range(a, kw + 2 * w, 2, true);
+            if (mk.val_write & (1u << w)) mark_range(a, vb + 2 * w, 2, true);
+            else if (mk.val_read & (1u << w)) mark_range(a, vb + 2 * w, 2, false);
+            if (mk.lru_write & (1u << w)) mark_range(a, lb + w, 1, true);
+        }
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) n_commit += __shfl_xor_sync(kFull, n_commit, w);
+    if (lane == 0 && n_commit) atomicAdd(a.counters + 0, n_commit);
+}
+
 }  // namespace
 
 cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks,
@@ -1014,6 +1119,7 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
     case 9: k_seg_exec<512><<<exec_blocks, 512 + 32, sizeof(SegSmem<512>), s>>>(o); break;
     default: return cudaErrorInvalidValue;
     }
+    k_cache_runs<<<stream_blocks, 256, 0, s>>>(o);
     return cudaGetLastError();
 }
 
