@@ -981,7 +981,33 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
     }
 }
 
-// One warp per cache run (see cache_apply).  Early validation's stop flag
+// Staging of every cache access's request in access-list order, so that the
+// run kernel reads it with coalesced loads instead of a chain of dependent
+// random ones (access -> record -> request).  It reuses scratch that is free
+// once the turns are computed: packed (key), runs (value), keys1 (batch << 1
+// | op), vals1 (index in the batch) and vals0 (the transaction's launch
+// index, which gives its commit version).
+__global__ void __launch_bounds__(256) k_cache_gather(OrderArgs o) {
+    const ExecArgs &a = o.e;
+    if (*o.n_cache_runs == 0) return;
+    const uint32_t n = *o.n_acc;
+    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += stride) {
+        const uint32_t v = o.vals0[j];
+        if (!(v & 2u)) continue;
+        const OrdRec &q = o.rec[v >> 4];
+        const uint32_t li = q.li, b = q.meta >> 16;
+        const hetm_cache_req r = static_cast<const hetm_cache_req *>(a.batches[b].tx)[li];
+        o.packed[j] = r.key;
+        o.runs[j] = r.value;
+        o.keys1[j] = (b << 1) | (r.op & 1u);
+        o.vals1[j] = li;
+        o.vals0[j] = q.u;
+    }
+}
+
+// One warp per cache run (see cache_apply); the next 32 staged requests are
+// loaded while the current ones are applied.  Early validation's stop flag
 // leaves runs not yet started as not run.
 __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
     const ExecArgs &a = o.e;
@@ -1021,33 +1047,72 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
         }
         uint32_t ver = (uint32_t)a.W[res], ver0 = ver, dirty_kv = 0, dirty_lru = 0;
         CacheMarks mk{};
-        for (uint32_t base = head;; base += 32) {
+        // staged request of lane `lane` in the chunk at `base`
+        auto stage = [&](uint32_t base, bool &in, uint64_t &key, uint64_t &value, uint32_t &meta,
+                         uint32_t &li, uint32_t &u) {
             const uint32_t j = base + lane;
-            const bool in = j < n_acc && o.keys0[j] == res;
-            const unsigned m = __ballot_sync(kFull, in);  // the run is contiguous: a prefix
-            uint64_t key = 0, value = 0;
-            uint32_t op = 0, li = 0, u = 0;
-            const DevBatch *d = nullptr;
+            in = j < n_acc && o.keys0[j] == res;  // the run is contiguous: a prefix of lanes
             if (in) {
-                const OrdRec &q = o.rec[o.vals0[j] >> 4];
-                li = q.li;
-                u = q.u;
-                d = a.batches + (q.meta >> 16);
-                const hetm_cache_req r = static_cast<const hetm_cache_req *>(d->tx)[li];
-                key = r.key;
-                value = r.value;
-                op = r.op & 1u;
+                key = o.packed[j];
+                value = o.runs[j];
+                meta = o.keys1[j];
+                li = o.vals1[j];
+                u = o.vals0[j];
             }
+        };
+        bool in = false, in_n = false;
+        uint64_t key = 0, value = 0, key_n = 0, value_n = 0;
+        uint32_t meta = 0, li = 0, u = 0, meta_n = 0, li_n = 0, u_n = 0;
+        stage(head, in, key, value, meta, li, u);
+        for (uint32_t base = head;; base += 32) {
+            const unsigned m = __ballot_sync(kFull, in);
             const int cnt = __popc(m);
+            if (cnt == 32) stage(base + 32, in_n, key_n, value_n, meta_n, li_n, u_n);
+            const uint32_t op = meta & 1u;
+            const DevBatch *d = in ? a.batches + (meta >> 1) : nullptr;
             uint64_t my_out = 0;
             if (!stopped) {
-                for (int l = 0; l < cnt; ++l) {
-                    const uint64_t k_ = shfl64(key, l), v_ = shfl64(value, l);
-                    const uint32_t op_ = __shfl_sync(kFull, op, l);
-                    const uint32_t stamp = (uint32_t)(v0 + 1 + __shfl_sync(kFull, u, l));
-                    const uint64_t out = cache_apply(keys, vals, lru, ver, dirty_kv, dirty_lru, k_, v_, op_,
-                                                     stamp, mk);
-                    if ((int)lane == l) my_out = out;
+                // GETs change no key or value, only stamps (by max): a stretch of
+                // GETs between two PUTs runs on all its lanes at once against
+                // the current copy; the PUTs are applied one at a time
+                const unsigned puts = __ballot_sync(kFull, in && op == 1u);
+                const uint32_t my_stamp = (uint32_t)(v0 + 1 + u);
+                int pos = 0;
+                while (pos < cnt) {
+                    const unsigned rest = puts & ~((1u << pos) - 1u);
+                    const int np = rest ? __ffs(rest) - 1 : cnt;  // next PUT (or the end)
+                    if (np > pos) {
+                        const bool get = (int)lane >= pos && (int)lane < np;
+                        int hit = -1;
+#pragma unroll
+                        for (int w = 7; w >= 0; --w)
+                            if (keys[w] == key) hit = w;
+                        if (get) {
+                            my_out = ~0ull;
+#pragma unroll
+                            for (int w = 0; w < 8; ++w)
+                                if (w == hit) my_out = vals[w];
+                        }
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) {
+                            const uint32_t sm_ = __reduce_max_sync(kFull, get && hit == w ? my_stamp : 0u);
+                            if (sm_) {
+                                lru[w] = max(lru[w], sm_);
+                                dirty_lru |= 1u << w;
+                                mk.val_read |= 1u << w;
+                                mk.lru_write |= 1u << w;
+                            }
+                        }
+                        mk.keys_read = 1;
+                    }
+                    if (np < cnt) {
+                        const uint64_t k_ = shfl64(key, np), v_ = shfl64(value, np);
+                        const uint32_t stamp = (uint32_t)__shfl_sync(kFull, my_stamp, np);
+                        const uint64_t out = cache_apply(keys, vals, lru, ver, dirty_kv, dirty_lru, k_, v_, 1u,
+                                                         stamp, mk);
+                        if ((int)lane == np) my_out = out;
+                    }
+                    pos = np + 1;
                 }
             }
             if (in) {
@@ -1061,6 +1126,12 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
             }
             if (!stopped) n_commit += in ? 1u : 0u;
             if (cnt < 32) break;
+            in = in_n;
+            key = key_n;
+            value = value_n;
+            meta = meta_n;
+            li = li_n;
+            u = u_n;
         }
         if (stopped) continue;
         // write back what changed: lane w owns way w
@@ -1119,6 +1190,7 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
     case 9: k_seg_exec<512><<<exec_blocks, 512 + 32, sizeof(SegSmem<512>), s>>>(o); break;
     default: return cudaErrorInvalidValue;
     }
+    k_cache_gather<<<stream_blocks, 256, 0, s>>>(o);
     k_cache_runs<<<stream_blocks, 256, 0, s>>>(o);
     return cudaGetLastError();
 }
