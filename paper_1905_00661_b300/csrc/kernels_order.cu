@@ -1093,16 +1093,18 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
                             for (int w = 0; w < 8; ++w)
                                 if (w == hit) my_out = vals[w];
                         }
-#pragma unroll
-                        for (int w = 0; w < 8; ++w) {
+                        // newest stamp per way hit, reduced over the ways actually hit
+                        const uint32_t ways = __reduce_or_sync(kFull, get && hit >= 0 ? 1u << hit : 0u);
+                        for (uint32_t wm = ways; wm; wm &= wm - 1u) {
+                            const int w = __ffs(wm) - 1;
                             const uint32_t sm_ = __reduce_max_sync(kFull, get && hit == w ? my_stamp : 0u);
-                            if (sm_) {
-                                lru[w] = max(lru[w], sm_);
-                                dirty_lru |= 1u << w;
-                                mk.val_read |= 1u << w;
-                                mk.lru_write |= 1u << w;
-                            }
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                if (k == w) lru[k] = max(lru[k], sm_);
                         }
+                        dirty_lru |= ways;
+                        mk.val_read |= ways;
+                        mk.lru_write |= ways;
                         mk.keys_read = 1;
                     }
                     if (np < cnt) {
