@@ -37,7 +37,7 @@ struct Scratch {                    // device-resident counters
     unsigned int stop;              // early validation: conflict seen, stop executing
     unsigned int segs_done;         //   ordered-phase segments finished
     unsigned int segs_total;        //   their number + 1 (0 = not known yet)
-    unsigned int pad2;
+    unsigned int exec_over;         //   nonzero once every executor kernel has finished
 };
 
 struct RoundOut {                   // pinned copy of the round's results
@@ -317,11 +317,13 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
         if (!per_batch) {
             o.e = exec_args(c, c->d_round, c->d_batches, c->d_prefix);
             if (c->early) {
-                CK(cudaMemsetAsync(&c->scr->stop, 0, 3 * sizeof(unsigned int), c->stream));
+                CK(cudaMemsetAsync(&c->scr->stop, 0, 4 * sizeof(unsigned int), c->stream));
                 if (capturing)
                     CK(cudaEventRecordWithFlags(c->ev_watch_start, c->stream, cudaEventRecordExternal));
             }
             CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream));
+            // stream order: set only after every kernel of the execution phase
+            if (c->early) CK(cudaMemsetAsync(&c->scr->exec_over, 0xFF, sizeof(unsigned int), c->stream));
             return HETM_OK;
         }
         for (uint32_t b = 0; b < nb; ++b) {
@@ -876,7 +878,7 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
         CK(cudaStreamWaitEvent(c->watch, c->ev_watch_start, 0));
         CK(cudaStreamWaitEvent(c->watch, c->ship_done, 0));
         CK(launch_watch(log, n, c->rs, c->gshift, c->n_words, &c->scr->stop, &c->scr->segs_done,
-                        &c->scr->segs_total, kWatchBudgetNs, c->n_sm, c->watch));
+                        &c->scr->segs_total, &c->scr->exec_over, kWatchBudgetNs, c->n_sm, c->watch));
         CK(cudaEventRecord(c->ev_watch_done, c->watch));
         CK(cudaStreamWaitEvent(c->stream, c->ev_watch_done, 0));
     }

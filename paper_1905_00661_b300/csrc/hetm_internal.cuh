@@ -200,8 +200,8 @@ __device__ __forceinline__ void rs_mark(uint32_t *rs, uint32_t *filter, uint64_t
 cudaError_t validate_setup();
 cudaError_t launch_watch(const hetm_log_entry *log, uint64_t n, const uint32_t *rs, uint32_t gshift,
                          uint64_t n_words, unsigned int *stop, const unsigned int *segs_done,
-                         const unsigned int *segs_total, unsigned long long budget_ns, int blocks,
-                         cudaStream_t s);
+                         const unsigned int *segs_total, const unsigned int *exec_over,
+                         unsigned long long budget_ns, int blocks, cudaStream_t s);
 cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
                             uint64_t n_words, uint32_t *flags, unsigned long long *count,
                             uint32_t *ts, int *err, const uint32_t *filter, int blocks,

@@ -208,12 +208,14 @@ __global__ void __launch_bounds__(kValThreads) k_validate_direct(const hetm_log_
 // watcher only saves the time of work that would be discarded.  It reads
 // RS_bmp through L2 (the executor's atomicOr lands there); a bit it misses
 // is caught by the final validation.  Every CTA leaves when the executor has
-// finished all its segments (*segs_done + 1 >= *segs_total), on a hit, or
-// after budget_ns.
+// finished all its segments (*segs_done + 1 >= *segs_total), when the
+// execution phase is over (*exec_over, set by the context stream after its
+// last kernel), on a hit, or after budget_ns.
 __global__ void __launch_bounds__(128) k_watch(const hetm_log_entry *__restrict__ log, uint64_t n,
                                                const uint32_t *rs, uint32_t gshift, uint64_t n_words,
                                                unsigned int *stop, const unsigned int *segs_done,
                                                const unsigned int *segs_total,
+                                               const unsigned int *exec_over,
                                                unsigned long long budget_ns) {
     __shared__ int s_quit;
     const unsigned long long t0 = globaltimer_ns();
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(128) k_watch(const hetm_log_entry *__restrict_
             const unsigned int tot = *(volatile const unsigned int *)segs_total;
             const unsigned int done = *(volatile const unsigned int *)segs_done;
             s_quit = *(volatile unsigned int *)stop != 0 || (tot != 0 && done + 1 >= tot) ||
-                     globaltimer_ns() - t0 > budget_ns;
+                     *(volatile const unsigned int *)exec_over != 0 || globaltimer_ns() - t0 > budget_ns;
         }
         __syncthreads();
         if (s_quit) return;
@@ -427,9 +429,10 @@ cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gsh
 
 cudaError_t launch_watch(const hetm_log_entry *log, uint64_t n, const uint32_t *rs, uint32_t gshift,
                          uint64_t n_words, unsigned int *stop, const unsigned int *segs_done,
-                         const unsigned int *segs_total, unsigned long long budget_ns, int blocks,
-                         cudaStream_t s) {
-    k_watch<<<blocks, 128, 0, s>>>(log, n, rs, gshift, n_words, stop, segs_done, segs_total, budget_ns);
+                         const unsigned int *segs_total, const unsigned int *exec_over,
+                         unsigned long long budget_ns, int blocks, cudaStream_t s) {
+    k_watch<<<blocks, 128, 0, s>>>(log, n, rs, gshift, n_words, stop, segs_done, segs_total, exec_over,
+                                   budget_ns);
     return cudaGetLastError();
 }
 
