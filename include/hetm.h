@@ -95,7 +95,10 @@ typedef struct hetm_rmw_tx {
  * the slot is set to the commit version; miss: out = UINT64_MAX.  PUT: hit
  * way, else the first empty way (key 0), else the way with the smallest GPU
  * LRU stamp (lowest way on ties) takes key and value, its stamp becomes the
- * commit version and the set version word is incremented; out = way. */
+ * commit version and the set version word is incremented; out = way.
+ * Requests conflict only with requests on the same set; word transactions
+ * (bank, W1) of the same execution phase must not address the cache regions
+ * (the ordered executor orders words and sets separately). */
 typedef struct hetm_cache_req {
     uint64_t key;
     uint64_t value;
