@@ -482,6 +482,16 @@ class Context:
         self._leave()
         return None
 
+    def round_wait(self):
+        """Wait for the round last started by ``round(stats=False)``; its stats."""
+        st = hetm_round_stats()
+        rc = _lib.hetm_round_wait(self.h, ctypes.byref(st))
+        d = st.as_dict()
+        d["rc"] = rc
+        if rc not in (HETM_OK, HETM_EDEVICE, HETM_ETIMEOUT):
+            raise HetmError(rc, "hetm_round_wait")
+        return d
+
 
 class Server:
     """Serving loop over a Context (continuous batching into rounds, see include/hetm.h).
