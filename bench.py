@@ -457,15 +457,21 @@ def critical_path(tx):
 
 
 def bench_w1_uniform(torch, h, init, update_frac, reps=3):
-    """The paper's W1 (Sec. V-A): 4 uniform words per transaction on the 2^28-word STMR."""
+    """The paper's W1 (Sec. V-A): 4 uniform words per transaction on the 2^28-word
+    STMR, run under the executor shape the autotuner picks for this batch."""
     tx = wl.rmw_batch(seed=SEED, batch=7, n_tx=N_TX, log2_words=LOG2W, uniform=True,
                       update_frac=update_frac)
-    with h.Context(1 << LOG2W, GRANULE, {"cpu_threads": 1}) as ctx:
+    dtx = torch.from_numpy(tx.view(np.uint8)).cuda()
+    o = torch.empty(N_TX, dtype=torch.int64, device="cuda")
+    st_ = torch.empty(N_TX, dtype=torch.uint8, device="cuda")
+    out = torch.empty(N_TX, dtype=torch.int32, device="cuda")
+    tuned = h.autotune(1 << LOG2W, init, [(h.HETM_WL_RMW, dtx, o, st_, out)],
+                       base={"cpu_threads": 1},
+                       space={"modes": 3, "threads": [128, 256, 512], "blocks_per_sm": [0],
+                              "lock_log2": [22, 24], "granules": [GRANULE],
+                              "ws_chunk_bytes": [16384], "reps": 2})
+    with h.Context(1 << LOG2W, GRANULE, dict({"cpu_threads": 1}, **tuned["config"])) as ctx:
         ctx.load(init)
-        dtx = torch.from_numpy(tx.view(np.uint8)).cuda()
-        o = torch.empty(N_TX, dtype=torch.int64, device="cuda")
-        st_ = torch.empty(N_TX, dtype=torch.uint8, device="cuda")
-        out = torch.empty(N_TX, dtype=torch.int32, device="cuda")
         ms = []
         for r in range(reps + 1):
             ctx.submit_batch(h.HETM_WL_RMW, dtx, o, st_, out, txid_base=r * N_TX, n_tx=N_TX)
@@ -474,7 +480,8 @@ def bench_w1_uniform(torch, h, init, update_frac, reps=3):
                 ms.append(st["ms_exec"])
     e = float(np.median(ms))
     upd = int(tx["flags"].sum())
-    return {"update_frac": update_frac, "exec_ms": e, "tx_per_s": N_TX / (e * 1e-3),
+    return {"update_frac": update_frac, "executor": tuned["config"],
+            "exec_ms": e, "tx_per_s": N_TX / (e * 1e-3),
             "exec_gbs": (16 * N_TX + 16 * upd) / (e * 1e-3) / 1e9,
             "word_reads": 4 * N_TX, "word_writes": 4 * upd}
 
