@@ -2,8 +2,9 @@
 //
 // All three stream an HBM-resident array once: the CPU write-set log (12-byte
 // tuples) for validate/apply, STMR^W and STMR^S on the dirty chunks for the
-// merge.  Loads are 16-byte vectors, non-allocating in L1, and every warp
-// keeps the next tile's loads in flight while it works on the current one.
+// merge.  Loads do not allocate in L1, and every warp keeps its next loads in
+// flight while it works on the current ones: apply and merge read 16-byte
+// vectors, validation reads only the tuple fields it tests.
 
 #include "hetm_internal.cuh"
 
@@ -55,13 +56,17 @@ __device__ __forceinline__ void tile_fields(const Tile &t, uint32_t a[4], int32_
 }
 
 // Shared-memory filter of RS_bmp.  Every random probe of the L2-resident
-// bitmap costs one 32-byte L2 sector, and at 16.8M probes per validation
-// those sectors, not HBM, bound the kernel.  Each CTA therefore first looks a
-// tuple's granule up in a 1M-bit hashed summary of the set granules (a Bloom
-// filter with one hash, maintained next to RS_bmp) kept in its shared
-// memory: a clear filter bit proves the granule is not in RS_bmp, and only
-// tuples whose filter bit is set probe L2.  A CTA uses the filter only while
-// at most 3/4 of its bits are set (else it would pass almost everything).
+// bitmap costs one 32-byte L2 sector and, while it is in flight, one L1
+// line of the SM, and at 16.8M probes per validation those probes bound the
+// kernel.  Each CTA therefore first looks a tuple's granule up in a 1M-bit
+// hashed summary of the set granules (a Bloom filter with one hash,
+// maintained next to RS_bmp) kept in its shared memory: a clear filter bit
+// proves the granule is not in RS_bmp, and only tuples whose filter bit is
+// set probe L2.  A CTA uses the filter only while at most 3/4 of its bits
+// are set (else it would pass almost everything).  The filter is not made
+// larger: the shared memory it takes comes out of the L1 lines that hold
+// the probes and log loads in flight, and a 1.5M- or 1.75M-bit filter made
+// the kernel slower on the validation-at-scale log.
 __device__ __forceinline__ const uint32_t *load_filter(const uint32_t *filter, uint32_t *smem) {
     __shared__ uint32_t s_fill;
     if (threadIdx.x == 0) s_fill = 0;
@@ -82,88 +87,114 @@ __device__ __forceinline__ const uint32_t *load_filter(const uint32_t *filter, u
     return s_fill <= kFilterBits / 4 * 3 ? smem : nullptr;
 }
 
-__device__ __forceinline__ uint32_t probe(const uint32_t *rs, const uint32_t *flt, uint32_t a,
-                                          uint32_t gshift) {
-    const uint32_t g = a >> gshift;
-    if (flt) {
-        const uint32_t sl = filter_slot(g);
-        if (!((flt[sl >> 5] >> (sl & 31)) & 1u)) return 0u;
-    }
-    return (__ldg(rs + (g >> 5)) >> (g & 31)) & 1u;
-}
-
 // Raise TS[a] to s.  A skewed log sends many tuples to a few hot words, and
 // atomics on one word serialize in its L2 slice; a tuple whose timestamp is
 // not above the value seen through L1 cannot change TS and skips the atomic.
 // TS only grows during the pass, so a stale cached value is at most the
 // current one: a skip is always safe, at worst an atomic is not saved.
-__device__ __forceinline__ void ts_raise(uint32_t *ts, uint32_t a, uint32_t s) {
+__device__ __forceinline__ uint32_t ts_seen(const uint32_t *ts, uint32_t a) {
     uint32_t seen;
     asm volatile("ld.global.ca.u32 %0, [%1];" : "=r"(seen) : "l"(ts + a));
-    if (seen < s) atomicMax(ts + a, s);
+    return seen;
+}
+__device__ __forceinline__ void ts_raise(uint32_t *ts, uint32_t a, uint32_t s) {
+    if (ts_seen(ts, a) < s) atomicMax(ts + a, s);
+}
+
+// 4-byte load of a log field that is read once (no L1 allocation)
+__device__ __forceinline__ uint32_t ld_field(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
 }
 
 // Validation (Sec. IV-C): flag = RS_bmp[granule(addr)] for every tuple, the
 // flags bit-packed in log order, the hits counted.  kMax additionally raises
 // TS[addr] to the tuple's timestamp (first pass of the apply).
+//
+// The log is read in groups of 32 consecutive tuples, lane l holding tuple
+// 32g + l: one 4-byte load per lane fetches the group's addresses (384
+// contiguous bytes, so each sector of the log crosses L2 once), and a warp
+// ballot over the group's probes is directly its flag word.  Only the fields
+// the pass uses are loaded (the timestamp only for kMax), and there is no
+// staging buffer, which leaves the shared memory to the filter.  Each warp
+// owns a contiguous range of groups and keeps kValGroups of them in flight:
+// the next kValGroups groups' loads are issued before the current ones are
+// probed.
+constexpr int kValGroups = 4;
+
 template <bool kMax>
 __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__ log, uint64_t n,
                                               const uint32_t *__restrict__ rs, uint32_t gshift,
                                               uint64_t n_words, uint32_t *__restrict__ flags,
                                               unsigned long long *count, uint32_t *ts, int *err,
-                                              const uint32_t *flt, uint4 *stage) {
+                                              const uint32_t *filter, uint32_t *s_filter) {
+    constexpr int U = kValGroups;
+    const uint32_t *lw = reinterpret_cast<const uint32_t *>(log);  // 3 words per tuple
     const unsigned lane = threadIdx.x & 31u;
-    stage += (threadIdx.x >> 5) * kTileVec;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = (gridDim.x * (uint64_t)blockDim.x) >> 5;
-    const uint64_t n_tiles = n / 128;
+    const uint64_t n_groups = (n + 31) / 32;
+    const uint64_t g0 = warp * n_groups / n_warps, g1 = (warp + 1) * n_groups / n_warps;
     uint32_t hits = 0;
     bool bad = false;
 
-    uint64_t c = warp;
-    Tile next;
-    if (c < n_tiles) next = load_tile(log, c, lane);
-    for (; c < n_tiles; c += n_warps) {
-        const Tile cur = own_tile(next, stage, lane);
-        if (c + n_warps < n_tiles) next = load_tile(log, c + n_warps, lane);
-        uint32_t a[4], s[4];
-        int32_t v[4];
-        tile_fields(cur, a, v, s);
-        uint32_t nib = 0;
+    uint32_t a[U], s[U];
+    bool v[U];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (a[j] < n_words) {
-                nib |= probe(rs, flt, a[j], gshift) << j;
-                if (kMax) ts_raise(ts, a[j], s[j]);
-            } else {
-                bad = true;
-            }
-        }
-        hits += __popc(nib);
-        // flag word k of the tile covers tuples 32k..32k+31 = lanes 8k..8k+7
-        uint32_t w = nib << (4u * (lane & 7u));
-        w |= __shfl_xor_sync(kFull, w, 1);
-        w |= __shfl_xor_sync(kFull, w, 2);
-        w |= __shfl_xor_sync(kFull, w, 4);
-        if (flags && (lane & 7u) == 0) flags[c * 4 + (lane >> 3)] = w;
+    for (int u = 0; u < U; ++u) {
+        const uint64_t t = (g0 + u) * 32 + lane;
+        v[u] = g0 + u < g1 && t < n;
+        a[u] = v[u] ? ld_field(lw + 3 * t) : 0u;
+        s[u] = kMax && v[u] ? ld_field(lw + 3 * t + 2) : 0u;
     }
-    // ragged tail (< 128 tuples): one warp, one tuple per lane per step
-    if (warp == n_warps - 1) {
-        for (uint64_t e0 = n_tiles * 128; e0 < n; e0 += 32) {
-            uint64_t i = e0 + lane;
-            uint32_t bit = 0;
-            if (i < n) {
-                uint32_t a = log[i].addr;
-                if (a < n_words) {
-                    bit = probe(rs, flt, a, gshift);
-                    if (kMax) ts_raise(ts, a, log[i].ts);
-                } else {
-                    bad = true;
-                }
+    // the filter is copied while the first groups' loads are in flight
+    const uint32_t *flt = load_filter(filter, s_filter);
+    for (uint64_t g = g0; g < g1; g += U) {
+        uint32_t na[U], ns[U];
+        bool nv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t t = (g + U + u) * 32 + lane;
+            nv[u] = g + U + u < g1 && t < n;
+            na[u] = nv[u] ? ld_field(lw + 3 * t) : 0u;
+            ns[u] = kMax && nv[u] ? ld_field(lw + 3 * t + 2) : 0u;
+        }
+        uint32_t gr[U], w[U];
+        bool in[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            in[u] = v[u] && a[u] < n_words;
+            bad |= v[u] && !in[u];
+            gr[u] = a[u] >> gshift;
+            bool p = in[u];
+            if (flt && p) {
+                const uint32_t sl = filter_slot(gr[u]);
+                p = (flt[sl >> 5] >> (sl & 31)) & 1u;
             }
-            uint32_t w = __ballot_sync(kFull, bit);
-            hits += bit;
-            if (flags && lane == 0) flags[e0 / 32] = w;
+            w[u] = p ? __ldg(rs + (gr[u] >> 5)) : 0u;
+        }
+        if (kMax) {
+            uint32_t seen[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) seen[u] = in[u] ? ts_seen(ts, a[u]) : ~0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (seen[u] < s[u]) atomicMax(ts + a[u], s[u]);
+        }
+        uint32_t mine = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t b = __ballot_sync(kFull, (w[u] >> (gr[u] & 31)) & 1u);
+            if (lane == (unsigned)u) mine = b;
+        }
+        hits += __popc(mine);
+        if (flags && lane < (unsigned)U && g + lane < g1) flags[g + lane] = mine;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[u] = na[u];
+            s[u] = ns[u];
+            v[u] = nv[u];
         }
     }
     if (bad) set_err(err, kErrAddr);
@@ -173,29 +204,25 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
 }
 
 template <bool kMax>
-__global__ void __launch_bounds__(kValThreads) k_validate_round(const DevRound *rp, const uint32_t *rs,
-                                                                uint32_t gshift, uint64_t n_words,
-                                                                uint32_t *flags,
-                                                                unsigned long long *count,
-                                                                uint32_t *ts, int *err,
-                                                                const uint32_t *filter) {
-    extern __shared__ uint4 s_dyn[];  // tile staging, then the filter
-    uint4 *stage = s_dyn;
-    const uint32_t *flt =
-        load_filter(filter, reinterpret_cast<uint32_t *>(s_dyn + kValThreads / 32 * kTileVec));
-    validate_body<kMax>(rp->log, rp->n_log, rs, gshift, n_words, flags, count, ts, err, flt, stage);
+__global__ void __launch_bounds__(kValThreads, 1) k_validate_round(const DevRound *rp, const uint32_t *rs,
+                                                                   uint32_t gshift, uint64_t n_words,
+                                                                   uint32_t *flags,
+                                                                   unsigned long long *count,
+                                                                   uint32_t *ts, int *err,
+                                                                   const uint32_t *filter) {
+    extern __shared__ uint4 s_dyn[];  // the filter
+    validate_body<kMax>(rp->log, rp->n_log, rs, gshift, n_words, flags, count, ts, err, filter,
+                        reinterpret_cast<uint32_t *>(s_dyn));
 }
 
-__global__ void __launch_bounds__(kValThreads) k_validate_direct(const hetm_log_entry *log, uint64_t n,
-                                                                 const uint32_t *rs, uint32_t gshift,
-                                                                 uint64_t n_words, uint32_t *flags,
-                                                                 unsigned long long *count, int *err,
-                                                                 const uint32_t *filter) {
-    extern __shared__ uint4 s_dyn[];  // tile staging, then the filter
-    uint4 *stage = s_dyn;
-    const uint32_t *flt =
-        load_filter(filter, reinterpret_cast<uint32_t *>(s_dyn + kValThreads / 32 * kTileVec));
-    validate_body<false>(log, n, rs, gshift, n_words, flags, count, nullptr, err, flt, stage);
+__global__ void __launch_bounds__(kValThreads, 1) k_validate_direct(const hetm_log_entry *log, uint64_t n,
+                                                                    const uint32_t *rs, uint32_t gshift,
+                                                                    uint64_t n_words, uint32_t *flags,
+                                                                    unsigned long long *count, int *err,
+                                                                    const uint32_t *filter) {
+    extern __shared__ uint4 s_dyn[];  // the filter
+    validate_body<false>(log, n, rs, gshift, n_words, flags, count, nullptr, err, filter,
+                         reinterpret_cast<uint32_t *>(s_dyn));
 }
 
 // Early validation (Sec. IV-D): while the ordered executor runs, the round's
@@ -400,7 +427,7 @@ __global__ void k_mark(const uint32_t *__restrict__ addr, const int32_t *__restr
 
 }  // namespace
 
-constexpr size_t kValSmem = kFilterBits / 8 + kValThreads / 32 * kTileVec * 16;
+constexpr size_t kValSmem = kFilterBits / 8;
 
 cudaError_t validate_setup() {
     const int smem = (int)kValSmem;
