@@ -639,8 +639,9 @@ template <uint32_t SEG>
 struct SegSmem {
     // (segment + 1) << 32 | value: one aligned 8-byte store hands a word on
     // to a later transaction of the segment, flag and data together
-    unsigned long long pack[SEG][4];  // this lane's output for slot k
-    unsigned long long ext[SEG][4];   // external input of slot k, from the poll warp
+    // slot-major, so that the lanes of a warp read 8-byte words 8 bytes apart
+    unsigned long long pack[4][SEG];  // output of thread t for slot k: pack[k][t]
+    unsigned long long ext[4][SEG];   // external input of slot k, from the poll warp
     uint32_t list_slot[SEG * 4];      // pending external slots: t << 2 | k
     uint32_t list_res[SEG * 4];       //   their resource
     uint32_t list_turn[SEG * 4];      //   their turn word
@@ -663,9 +664,9 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
     unsigned long long n_commit = 0, n_gaveup = 0;
     if (!poller) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sm.pack[t][k] = 0ull;
+        for (int k = 0; k < 4; ++k) sm.pack[k][t] = 0ull;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sm.ext[t][k] = 0ull;
+        for (int k = 0; k < 4; ++k) sm.ext[k][t] = 0ull;
     }
     if (t == 0) sm.abort = 0;
     if (t == 0 && blockIdx.x == 0 && a.segs_total) st_rlx32((int32_t *)a.segs_total, (int32_t)(n_seg + 1));
@@ -744,7 +745,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         if (ok[j])
-                            *(volatile unsigned long long *)&sm.ext[sl[j] >> 2][sl[j] & 3u] =
+                            *(volatile unsigned long long *)&sm.ext[sl[j] & 3u][sl[j] >> 2] =
                                 tag | (uint32_t)pv[j];
                     __syncwarp();
                     // compact the pending entries in place (writes land below
@@ -859,11 +860,49 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         uint32_t pend = ext | loc;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const unsigned long long *w = &sm.pack[t][k];
-            if (loc & (1u << k)) w = &sm.pack[rc.src[k] >> 2][rc.src[k] & 3u];
-            else if (ext & (1u << k)) w = &sm.ext[t][k];
+            const unsigned long long *w = &sm.pack[k][t];
+            if (loc & (1u << k)) w = &sm.pack[rc.src[k] & 3u][rc.src[k] >> 2];
+            else if (ext & (1u << k)) w = &sm.ext[k][t];
             watch[k] = (uint32_t)__cvta_generic_to_shared(w);
         }
+        auto run_tx = [&]() {
+            if (rmw4) {
+                sum = cur[0] + cur[1] + cur[2] + cur[3];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) nv[k] = sum + k + (int32_t)rc.aux;
+            } else if (wl == HETM_WL_RMW) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t sl = (rc.meta >> (8 + 2 * j)) & 3u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if ((uint32_t)k == sl) sum += cur[k];
+                }
+                // a word named twice keeps the value of its last position
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t sl = (rc.meta >> (8 + 2 * j)) & 3u;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if ((uint32_t)k == sl) nv[k] = sum + j + (int32_t)rc.aux;
+                }
+            } else if (n == 1) {  // bank transfer onto the same account
+                nv[0] = cur[0];
+            } else {
+                nv[0] = cur[0] - (int32_t)rc.aux;
+                nv[1] = cur[1] + (int32_t)rc.aux;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < (int)n) *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < (int)n && (rc.turn[k] & kFPublish))
+                    st_rlx64(o.packed + rc.res[k],
+                             ((unsigned long long)((rc.turn[k] & kTurnMask) + 1) << 32) | (uint32_t)nv[k]);
+            finished = true;
+            executed = true;
+        };
         uint32_t idle = 0, checks = 0;
         for (;;) {
             unsigned long long v[4];
@@ -877,46 +916,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 pend &= got ? ~(1u << k) : ~0u;
             }
             const bool ready = !finished && pend == 0;
-            if (ready) {
-                if (rmw4) {
-                    sum = cur[0] + cur[1] + cur[2] + cur[3];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) nv[k] = sum + k + (int32_t)rc.aux;
-                } else if (wl == HETM_WL_RMW) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t sl = (rc.meta >> (8 + 2 * j)) & 3u;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if ((uint32_t)k == sl) sum += cur[k];
-                    }
-                    // a word named twice keeps the value of its last position
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint32_t sl = (rc.meta >> (8 + 2 * j)) & 3u;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            if ((uint32_t)k == sl) nv[k] = sum + j + (int32_t)rc.aux;
-                    }
-                } else if (n == 1) {  // bank transfer onto the same account
-                    nv[0] = cur[0];
-                } else {
-                    nv[0] = cur[0] - (int32_t)rc.aux;
-                    nv[1] = cur[1] + (int32_t)rc.aux;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < (int)n)
-                        *(volatile unsigned long long *)&sm.pack[t][k] = tag | (uint32_t)nv[k];
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < (int)n && (rc.turn[k] & kFPublish))
-                        st_rlx64(o.packed + rc.res[k],
-                                 ((unsigned long long)((rc.turn[k] & kTurnMask) + 1) << 32) |
-                                     (uint32_t)nv[k]);
-                finished = true;
-                executed = true;
-            }
+            if (ready) run_tx();
             __syncwarp();
             if (__all_sync(kFull, finished)) break;
             if (__any_sync(kFull, ready)) {
@@ -963,7 +963,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 sm.abort = 1;
                 // release local successors so that they end too
 #pragma unroll
-                for (int k = 0; k < 4; ++k) *(volatile unsigned long long *)&sm.pack[t][k] = tag;
+                for (int k = 0; k < 4; ++k) *(volatile unsigned long long *)&sm.pack[k][t] = tag;
             }
         }
         __syncthreads();  // end of segment
