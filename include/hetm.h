@@ -55,7 +55,8 @@ extern "C" {
 #define HETM_ECUDA (-5)     /* a CUDA runtime call failed                     */
 #define HETM_EBUSY (-6)     /* not admitted now (memory or slots); retry later */
 #define HETM_EDEVICE (-7)   /* a kernel met an out-of-range address; the
-                               offending item was skipped, state is undefined */
+                               offending item was skipped, state is undefined;
+                               the context keeps reporting it until hetm_load */
 
 HETM_API const char *hetm_strerror(int code);
 
