@@ -350,6 +350,34 @@ HETM_API int hetm_round(hetm_ctx *ctx, hetm_round_stats *stats);
  * (may be NULL).  Returns the round's status like hetm_round. */
 HETM_API int hetm_round_wait(hetm_ctx *ctx, hetm_round_stats *stats);
 
+/* Where a submitted batch is, without blocking (the GPU-controller's view of
+ * its queue, Sec. III-A: a transactional kernel's requests finish when the
+ * synchronization round that ran them has merged).  A batch is QUEUED until
+ * hetm_gpu_exec or hetm_round launches it, RUNNING until the round that ran
+ * it has finished its merge on the device (hetm_round, or hetm_merge after
+ * hetm_gpu_exec and hetm_validate), then DONE: its order, status and out
+ * buffers hold their final values, `outcome` is that round's HETM_OUTCOME_*
+ * (HETM_OUTCOME_UNKNOWN when it ended more than 64 rounds before the first
+ * poll that saw it done) and `latency_ms` is host time from its submission
+ * to that first poll.  Ids are those hetm_gpu_submit_batch returned; the
+ * context remembers the last 65,536 batches, and forgets those that
+ * hetm_load discarded.  HETM_EINVAL for an unknown id or NULL pointer,
+ * HETM_ECUDA if the device query failed.  Call from the controller thread. */
+#define HETM_BATCH_QUEUED 1
+#define HETM_BATCH_RUNNING 2
+#define HETM_BATCH_DONE 3
+#define HETM_OUTCOME_UNKNOWN 0xFFFFFFFFu
+typedef struct {
+    uint32_t state;      /* HETM_BATCH_QUEUED / _RUNNING / _DONE             */
+    uint32_t outcome;    /* DONE: the round's HETM_OUTCOME_* (else 0)        */
+    uint64_t round;      /* sequence number of the round that runs it, 0 while queued */
+    uint32_t n_tx;       /* transactions of the batch                        */
+    uint32_t reserved;
+    double latency_ms;   /* DONE: submission -> first poll that saw it done  */
+} hetm_batch_result;
+
+HETM_API int hetm_batch_poll(hetm_ctx *ctx, uint64_t batch_id, hetm_batch_result *out);
+
 /* Host side of the merge (Sec. IV-C merge phase, Sec. IV-E): copy into the
  * host replica `host_stmr` (stmr_words int32, host memory) every WS_bmp
  * chunk of the last completed round whose GPU writes survived it (a clean

@@ -26,6 +26,8 @@ HETM_WL_BANK, HETM_WL_RMW, HETM_WL_CACHE = 1, 2, 3
 HETM_POLICY_GPU_LOSES, HETM_POLICY_CPU_LOSES = 0, 1
 HETM_OUTCOME_CLEAN, HETM_OUTCOME_GPU_ROLLED_BACK, HETM_OUTCOME_CPU_DISCARDED = 0, 1, 2
 HETM_EXEC_ORDERED, HETM_EXEC_OPTIMISTIC = 0, 1
+HETM_BATCH_QUEUED, HETM_BATCH_RUNNING, HETM_BATCH_DONE = 1, 2, 3
+HETM_OUTCOME_UNKNOWN = 0xFFFFFFFF
 STMR_W, STMR_S, TS, RS_BMP, WS_BMP = 0, 1, 2, 3, 4
 
 LOG_DTYPE = np.dtype([("addr", "<u4"), ("value", "<i4"), ("ts", "<u4")])
@@ -52,6 +54,14 @@ class hetm_batch(ctypes.Structure):
                 ("out", _vp), ("txid_base", _u32), ("word_base", _u32)]
 
 
+class hetm_batch_result(ctypes.Structure):
+    _fields_ = [("state", _u32), ("outcome", _u32), ("round", _u64), ("n_tx", _u32),
+                ("reserved", _u32), ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class hetm_round_stats(ctypes.Structure):
     _fields_ = [("n_log", _u64), ("n_conflicts", _u64), ("conflict", _i32), ("err", _i32),
                 ("committed", _u64), ("gave_up", _u64), ("aborts", _u64), ("dirty_chunks", _u64),
@@ -74,7 +84,7 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
            "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune",
            "hetm_handoff_latency", "hetm_random_access_rate", "hetm_read_dirty",
-           "hetm_cpu_updates_allowed")
+           "hetm_cpu_updates_allowed", "hetm_batch_poll")
 
 
 class hetm_tune_space(ctypes.Structure):
@@ -144,6 +154,7 @@ def _declare(L):
         "hetm_validate_noalloc": (_int, [_vp, _u64, _vp, _u32, _u64, _vp, _vp, _vp, _vp]),
         "hetm_ctx_stream": (_vp, [_vp]),
         "hetm_round_wait": (_int, [_vp, P(hetm_round_stats)]),
+        "hetm_batch_poll": (_int, [_vp, _u64, P(hetm_batch_result)]),
         "hetm_server_config_default": (_int, [P(hetm_server_config)]),
         "hetm_server_create": (_int, [P(_vp), _vp, P(hetm_server_config)]),
         "hetm_server_submit": (_int, [_vp, P(hetm_request), P(_u64)]),
@@ -491,6 +502,13 @@ class Context:
         if rc not in (HETM_OK, HETM_EDEVICE, HETM_ETIMEOUT):
             raise HetmError(rc, "hetm_round_wait")
         return d
+
+    def batch_poll(self, batch_id):
+        """State of a submitted batch without blocking (HETM_BATCH_*), the outcome
+        of the round that ran it, its round number and its latency once done."""
+        r = hetm_batch_result()
+        _ck(_lib.hetm_batch_poll(self.h, int(batch_id), ctypes.byref(r)), "hetm_batch_poll")
+        return r.as_dict()
 
 
 class Server:

@@ -11,8 +11,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -66,6 +68,9 @@ bool pow2(uint64_t v) { return v && !(v & (v - 1)); }
 
 }  // namespace
 
+constexpr int kRoundRing = 64;        // rounds whose end hetm_batch_poll can still look up
+constexpr size_t kBatchRecs = 65536;  // batches hetm_batch_poll keeps track of
+
 struct hetm_ctx {
     int device = 0;
     int n_sm = 0;
@@ -99,7 +104,27 @@ struct hetm_ctx {
     RoundOut *out = nullptr;       // pinned
 
     std::vector<DevBatch> pending;
+    std::vector<uint64_t> pending_ids;  // ids of `pending`, same order
     uint64_t next_batch_id = 1;
+
+    // batch tracking for hetm_batch_poll: every round that runs batches gets a
+    // sequence number; its end (after the merge) records an event and a pinned
+    // copy of its conflict count in slot seq % kRoundRing
+    struct BatchRec {
+        uint32_t n_tx = 0;
+        uint64_t round = 0;  // 0 while queued
+        bool done = false;
+        uint32_t outcome = 0;
+        double latency_ms = 0;
+        std::chrono::steady_clock::time_point t_submit;
+    };
+    std::map<uint64_t, BatchRec> brec;
+    uint64_t round_seq = 0;             // rounds that ran batches so far
+    uint64_t exec_round = 0;            // round whose execution ran, not merged yet (0: none)
+    cudaEvent_t rend[kRoundRing] = {};  // end of round seq, slot seq % kRoundRing
+    uint64_t rend_seq[kRoundRing] = {};
+    int rend_force[kRoundRing] = {};    // conflict decided by the caller (-1: counted)
+    unsigned long long *rconf = nullptr; // pinned: hits of round seq, same slot
 
     // CPU logs
     std::vector<std::unique_ptr<ThreadLog>> tlogs;
@@ -486,6 +511,9 @@ void hetm_destroy(hetm_ctx *c) {
         for (auto *b : L->buf)
             if (b) cudaFreeHost(b);
     if (c->out) cudaFreeHost(c->out);
+    if (c->rconf) cudaFreeHost(c->rconf);
+    for (auto &e : c->rend)
+        if (e) cudaEventDestroy(e);
     if (c->ws_host) cudaFreeHost(c->ws_host);
     for (void *p : c->dev_allocs) {
         if (c->cfg.dev_free) c->cfg.dev_free(p, c->cfg.alloc_user);
@@ -604,6 +632,10 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         return fail(HETM_ECUDA);
     for (auto &e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return fail(HETM_ECUDA);
+    for (auto &e : c->rend)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(HETM_ECUDA);
+    if (!host_alloc_t(&c->rconf, kRoundRing)) return fail(HETM_ENOMEM);
+    std::memset(c->rconf, 0, kRoundRing * sizeof(unsigned long long));
     for (uint32_t t = 0; t < d.cpu_threads; ++t) c->tlogs.emplace_back(new ThreadLog());
 
     int occ = 0;
@@ -658,6 +690,15 @@ int hetm_load(hetm_ctx *c, const int32_t *src, uint64_t n) {
     }
     c->dlog_fill.store(0);
     c->pending.clear();
+    // batches still queued, or run by an execution phase that never merged,
+    // are discarded with the state: hetm_batch_poll forgets them
+    for (uint64_t id : c->pending_ids) c->brec.erase(id);
+    c->pending_ids.clear();
+    if (c->exec_round) {
+        for (auto it = c->brec.begin(); it != c->brec.end();)
+            it = it->second.round == c->exec_round ? c->brec.erase(it) : std::next(it);
+        c->exec_round = 0;
+    }
     c->attached = nullptr;
     c->attached_n = 0;
     std::memset(c->prev_counters, 0, sizeof(c->prev_counters));
@@ -725,7 +766,35 @@ int hetm_gpu_submit_batch(hetm_ctx *c, const hetm_batch *b, uint64_t *batch_id) 
     }
     DevBatch d{b->workload, b->n_tx, b->tx, b->order, b->status, b->out, b->txid_base, b->word_base};
     c->pending.push_back(d);
-    if (batch_id) *batch_id = c->next_batch_id++;
+    const uint64_t id = c->next_batch_id++;
+    c->pending_ids.push_back(id);
+    hetm_ctx::BatchRec rec;
+    rec.n_tx = b->n_tx;
+    rec.t_submit = std::chrono::steady_clock::now();
+    c->brec.emplace(id, rec);
+    while (c->brec.size() > kBatchRecs) c->brec.erase(c->brec.begin());
+    if (batch_id) *batch_id = id;
+    return HETM_OK;
+}
+
+// The queued batches join round `r` (their execution phase is being launched).
+static void assign_round(hetm_ctx *c, uint64_t r) {
+    for (uint64_t id : c->pending_ids) {
+        auto it = c->brec.find(id);
+        if (it != c->brec.end()) it->second.round = r;
+    }
+    c->pending_ids.clear();
+}
+
+// End of round `r` on the context stream (after its merge): its event and the
+// conflict count of its validation (or the caller's decision, force >= 0).
+static int end_round(hetm_ctx *c, uint64_t r, int force) {
+    const int slot = (int)(r % kRoundRing);
+    CK(cudaMemcpyAsync(&c->rconf[slot], &c->scr->conflicts, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(c->rend[slot], c->stream));
+    c->rend_seq[slot] = r;
+    c->rend_force[slot] = force;
     return HETM_OK;
 }
 
@@ -737,6 +806,8 @@ int hetm_gpu_exec(hetm_ctx *c, int per_batch) {
     if (rc != HETM_OK) return rc;
     rc = enqueue_exec(c, per_batch != 0, (uint32_t)c->pending.size());
     c->pending.clear();
+    if (!c->exec_round) c->exec_round = ++c->round_seq;
+    assign_round(c, c->exec_round);
     return rc;
 }
 
@@ -843,6 +914,11 @@ int hetm_merge(hetm_ctx *c, int conflict) {
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
     CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
+    if (c->exec_round) {
+        const int rc = end_round(c, c->exec_round, conflict);
+        c->exec_round = 0;
+        if (rc != HETM_OK) return rc;
+    }
     return HETM_OK;
 }
 
@@ -865,6 +941,10 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
     if (nb) CK(cudaGraphLaunch(c->g_exec, c->stream));
     CK(cudaEventRecord(c->ev[6], c->stream));
     c->pending.clear();
+    if (nb || c->exec_round) {
+        if (!c->exec_round) c->exec_round = ++c->round_seq;
+        assign_round(c, c->exec_round);
+    }
     // end of the execution phase: ship the rest of the logs, then validate
     const hetm_log_entry *log = nullptr;
     uint64_t n = 0;
@@ -885,6 +965,11 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
     CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
     CK(cudaGraphLaunch(c->g_sync, c->stream));
     CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
+    if (c->exec_round) {
+        rc = end_round(c, c->exec_round, c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES ? 0 : -1);
+        c->exec_round = 0;
+        if (rc != HETM_OK) return rc;
+    }
     CK(cudaEventRecord(c->ev[5], c->stream));
     c->last_n_log = n;
     c->last_nb = nb;
@@ -971,6 +1056,44 @@ int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     if (cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]) == cudaSuccess) stats->ms_merge = ms;
     if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]) == cudaSuccess) stats->ms_total = ms;
     return stats->err;
+}
+
+int hetm_batch_poll(hetm_ctx *c, uint64_t batch_id, hetm_batch_result *out) {
+    if (!c || !out) return HETM_EINVAL;
+    auto it = c->brec.find(batch_id);
+    if (it == c->brec.end()) return HETM_EINVAL;
+    hetm_ctx::BatchRec &b = it->second;
+    std::memset(out, 0, sizeof(*out));
+    out->n_tx = b.n_tx;
+    out->round = b.round;
+    if (!b.done && b.round) {
+        const int slot = (int)(b.round % kRoundRing);
+        if (c->rend_seq[slot] > b.round) {
+            // a later round ended in this slot, so this one ended before it
+            b.done = true;
+            b.outcome = HETM_OUTCOME_UNKNOWN;
+        } else if (c->rend_seq[slot] == b.round) {
+            if (cudaSetDevice(c->device) != cudaSuccess) return HETM_ECUDA;
+            const cudaError_t q = cudaEventQuery(c->rend[slot]);
+            if (q == cudaSuccess) {
+                const int f = c->rend_force[slot];
+                const bool conflict = f >= 0 ? f != 0 : c->rconf[slot] != 0;
+                const bool cpu_loses = c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES;
+                b.done = true;
+                b.outcome = !conflict ? HETM_OUTCOME_CLEAN
+                                      : (cpu_loses ? HETM_OUTCOME_CPU_DISCARDED : HETM_OUTCOME_GPU_ROLLED_BACK);
+            } else if (q != cudaErrorNotReady) {
+                return HETM_ECUDA;
+            }
+        }
+        if (b.done)
+            b.latency_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                                     b.t_submit).count();
+    }
+    out->state = !b.round ? HETM_BATCH_QUEUED : (b.done ? HETM_BATCH_DONE : HETM_BATCH_RUNNING);
+    out->outcome = b.done ? b.outcome : 0u;
+    out->latency_ms = b.done ? b.latency_ms : 0.0;
+    return HETM_OK;
 }
 
 }  // extern "C"

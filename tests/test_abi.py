@@ -122,3 +122,12 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         assert int(got[n]) == ctypes.sizeof(st), n
         for f, _ in st._fields_:
             assert int(got[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"
+
+
+def test_batch_poll_rejects_bad_arguments_without_gpu():
+    import paper_1905_00661_b300 as h
+    L = h.lib()
+    r = h.hetm_batch_result()
+    assert L.hetm_batch_poll(None, 1, ctypes.byref(r)) == h.HETM_EINVAL
+    assert L.hetm_batch_poll(None, 1, None) == h.HETM_EINVAL
+    assert ctypes.sizeof(h.hetm_batch_result) == 32
