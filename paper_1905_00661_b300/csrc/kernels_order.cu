@@ -1060,6 +1060,22 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
                 u = o.vals0[j];
             }
         };
+        // GPU stamps only grow, and stamps grow with the rank, so a way's
+        // stamp is the largest stamp of any access to it.  A GET therefore
+        // only raises this lane's own running maximum for the way it hit;
+        // the lanes' maxima are folded into the set copy (warp reductions)
+        // only where a stamp is read: before a PUT that must evict, and at
+        // the end of the run.
+        uint32_t pl[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // this lane's newest GET stamp per way
+        uint32_t pend_ways = 0, mark_ways = 0;        // ways with unfolded stamps / hit by this lane
+        bool any_get = false;
+        auto fold = [&]() {
+            const uint32_t wa = __reduce_or_sync(kFull, pend_ways);
+#pragma unroll
+            for (int w = 0; w < 8; ++w)
+                if ((wa >> w) & 1u) lru[w] = max(lru[w], __reduce_max_sync(kFull, pl[w]));
+            pend_ways = 0;
+        };
         bool in = false, in_n = false;
         uint64_t key = 0, value = 0, key_n = 0, value_n = 0;
         uint32_t meta = 0, li = 0, u = 0, meta_n = 0, li_n = 0, u_n = 0;
@@ -1089,27 +1105,29 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
                             if (keys[w] == key) hit = w;
                         if (get) {
                             my_out = ~0ull;
+                            any_get = true;
 #pragma unroll
                             for (int w = 0; w < 8; ++w)
-                                if (w == hit) my_out = vals[w];
+                                if (w == hit) {
+                                    my_out = vals[w];
+                                    pl[w] = max(pl[w], my_stamp);
+                                }
+                            if (hit >= 0) {
+                                pend_ways |= 1u << hit;
+                                mark_ways |= 1u << hit;
+                            }
                         }
-                        // newest stamp per way hit, reduced over the ways actually hit
-                        const uint32_t ways = __reduce_or_sync(kFull, get && hit >= 0 ? 1u << hit : 0u);
-                        for (uint32_t wm = ways; wm; wm &= wm - 1u) {
-                            const int w = __ffs(wm) - 1;
-                            const uint32_t sm_ = __reduce_max_sync(kFull, get && hit == w ? my_stamp : 0u);
-#pragma unroll
-                            for (int k = 0; k < 8; ++k)
-                                if (k == w) lru[k] = max(lru[k], sm_);
-                        }
-                        dirty_lru |= ways;
-                        mk.val_read |= ways;
-                        mk.lru_write |= ways;
-                        mk.keys_read = 1;
                     }
                     if (np < cnt) {
                         const uint64_t k_ = shfl64(key, np), v_ = shfl64(value, np);
                         const uint32_t stamp = (uint32_t)__shfl_sync(kFull, my_stamp, np);
+                        // a PUT that neither hits nor finds an empty way evicts by
+                        // stamp: bring the stamps up to date first (warp-uniform:
+                        // every lane holds the same copy)
+                        bool hit_or_empty = false;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) hit_or_empty |= keys[w] == k_ || keys[w] == 0;
+                        if (!hit_or_empty) fold();
                         const uint64_t out = cache_apply(keys, vals, lru, ver, dirty_kv, dirty_lru, k_, v_, 1u,
                                                          stamp, mk);
                         if ((int)lane == np) my_out = out;
@@ -1136,6 +1154,14 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
             u = u_n;
         }
         if (stopped) continue;
+        fold();
+        {
+            const uint32_t wm = __reduce_or_sync(kFull, mark_ways);
+            dirty_lru |= wm;
+            mk.val_read |= wm;
+            mk.lru_write |= wm;
+            if (__any_sync(kFull, any_get)) mk.keys_read = 1;
+        }
         // write back what changed: lane w owns way w
         if (lane < 8) {
 #pragma unroll
