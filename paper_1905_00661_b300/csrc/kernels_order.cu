@@ -1087,12 +1087,62 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
             const uint32_t op = meta & 1u;
             const DevBatch *d = in ? a.batches + (meta >> 1) : nullptr;
             uint64_t my_out = 0;
-            if (!stopped) {
+            // every lane looks its own key up in the copy as it is at the chunk's start
+            int h0 = -1;
+#pragma unroll
+            for (int w = 7; w >= 0; --w)
+                if (keys[w] == key) h0 = w;
+            const unsigned puts = __ballot_sync(kFull, in && op == 1u);
+            const uint32_t my_stamp = (uint32_t)(v0 + 1 + u);
+            if (!stopped && !__any_sync(kFull, in && op == 1u && h0 < 0)) {
+                // Every PUT of the chunk updates a key already in the set, in
+                // place: no key moves, so each GET reads the value of the last
+                // PUT to its way before it in the chunk, else the chunk-start
+                // copy, and each way written ends with its last PUT's value.
+                const unsigned same = __match_any_sync(kFull, in ? h0 : -2);
+                const unsigned before = same & puts & lanemask_lt();
+                const int src = before ? 31 - __clz(before) : (int)lane;
+                const uint64_t pv = shfl64(value, src);
+                if (in) {
+                    if (op == 1u) {
+                        my_out = (uint64_t)h0;
+                    } else {
+                        uint64_t cv = ~0ull;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w)
+                            if (w == h0) cv = vals[w];
+                        my_out = before ? pv : cv;
+                        any_get = true;
+                        if (h0 >= 0) mark_ways |= 1u << h0;
+                    }
+                    if (h0 >= 0) {
+#pragma unroll
+                        for (int w = 0; w < 8; ++w)
+                            if (w == h0) pl[w] = max(pl[w], my_stamp);
+                        pend_ways |= 1u << h0;
+                    }
+                }
+                if (puts) {
+                    const bool last_put = ((puts >> lane) & 1u) && !(same & puts & ~lanemask_lt() & ~(1u << lane));
+                    const uint32_t wput = __reduce_or_sync(kFull, last_put ? 1u << h0 : 0u);
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        if (!((wput >> w) & 1u)) continue;
+                        const unsigned lb = __ballot_sync(kFull, last_put && h0 == w);
+                        vals[w] = shfl64(value, __ffs(lb) - 1);
+                    }
+                    dirty_kv |= wput;
+                    dirty_lru |= wput;
+                    mk.val_write |= wput;
+                    mk.lru_write |= wput;
+                    mk.ver_write = 1;
+                    ver += (uint32_t)__popc(puts);
+                }
+                if (cnt) mk.keys_read = 1;
+            } else if (!stopped) {
                 // GETs change no key or value, only stamps (by max): a stretch of
                 // GETs between two PUTs runs on all its lanes at once against
                 // the current copy; the PUTs are applied one at a time
-                const unsigned puts = __ballot_sync(kFull, in && op == 1u);
-                const uint32_t my_stamp = (uint32_t)(v0 + 1 + u);
                 int pos = 0;
                 while (pos < cnt) {
                     const unsigned rest = puts & ~((1u << pos) - 1u);

@@ -324,3 +324,57 @@ def test_whole_stmr_granule_conflicts(hetm, torch, mode):
                                                       4 * n)
         ref = _finish_round(ctx, h, torch, start, replayed, R, log, 4 * n)
         assert ref.conflict and ref.final[5] == 1
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_cache_one_hot_set_chunks(hetm, torch, mode):
+    """One set, requests in launch order over whole 32-request chunks: chunks whose
+    PUTs all update keys already in the set (GETs then read the newest value
+    written to their way earlier in the chunk), and chunks with a PUT of an absent
+    key into the full set (an eviction by stamp), followed by GETs of the new and
+    the evicted key.  Outputs and the final STMR against the oracle's replay."""
+    h = hetm
+    lay = wl.CacheLayout(log2_sets=4)
+    start = wl.cache_prefill(lay, 512)
+    keys_of_set = start[lay.key_base: lay.val_base].view(np.uint64).reshape(lay.n_sets, 8)
+    s = 5
+    present = [int(k) for k in keys_of_set[s]]
+    assert all(present) and len(set(present)) == 8
+    allk = np.arange(1, 4096, dtype=np.uint64)
+    absent = [int(k) for k in allk[wl.set_of_key(allk, lay.log2_sets) == s] if int(k) not in present][:3]
+    k1, k2 = present[2], present[6]
+    seq = []
+    # chunk 1 and 2: PUTs that hit, GETs between them on the same and other ways
+    for i in range(64):
+        r = i % 8
+        if r in (1, 5):
+            seq.append((k1, 1000 + i, 1))
+        elif r == 3:
+            seq.append((k2, 2000 + i, 1))
+        elif r == 7:
+            seq.append((absent[0] if i % 16 == 7 else k2, 0, 0))
+        else:
+            seq.append((k1 if r % 2 == 0 else present[i % 8], 0, 0))
+    # chunk 3: an eviction in the middle, then GETs of the new and an evicted key
+    for i in range(32):
+        if i == 10:
+            seq.append((absent[1], 777, 1))
+        elif i == 20:
+            seq.append((absent[2], 888, 1))
+        elif i % 3 == 0:
+            seq.append((k1, 3000 + i, 1))
+        else:
+            seq.append(((absent[1], present[0], absent[2], k2)[i % 4], 0, 0))
+    reqs = np.zeros(len(seq), dtype=wl.CACHE_DTYPE)
+    reqs["key"] = [k for k, _, _ in seq]
+    reqs["value"] = [v for _, v, _ in seq]
+    reqs["op"] = [op for _, _, op in seq]
+    cfg = {"lock_shift": 4, "cache_log2_sets": lay.log2_sets, "cache_key_base": lay.key_base,
+           "cache_val_base": lay.val_base, "cache_lru_base": lay.gpu_lru_base,
+           "cache_ver_base": lay.ver_base, "ws_chunk_bytes": 64, "exec_mode": mode}
+    with h.Context(lay.n_words, 64, cfg) as ctx:
+        ctx.load(start)
+        bo = submit(ctx, torch, wl.WORKLOAD_CACHE, reqs)
+        _, _, _, _, stat = _exec_and_check_replay(ctx, h, torch, start, [(reqs, bo, 0)], 64, 64,
+                                                  kind="cache", layout=lay)
+        assert (stat == 1).all()
