@@ -1087,97 +1087,80 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
             const uint32_t op = meta & 1u;
             const DevBatch *d = in ? a.batches + (meta >> 1) : nullptr;
             uint64_t my_out = 0;
-            // every lane looks its own key up in the copy as it is at the chunk's start
-            int h0 = -1;
-#pragma unroll
-            for (int w = 7; w >= 0; --w)
-                if (keys[w] == key) h0 = w;
             const unsigned puts = __ballot_sync(kFull, in && op == 1u);
             const uint32_t my_stamp = (uint32_t)(v0 + 1 + u);
-            if (!stopped && !__any_sync(kFull, in && op == 1u && h0 < 0)) {
-                // Every PUT of the chunk updates a key already in the set, in
-                // place: no key moves, so each GET reads the value of the last
-                // PUT to its way before it in the chunk, else the chunk-start
-                // copy, and each way written ends with its last PUT's value.
-                const unsigned same = __match_any_sync(kFull, in ? h0 : -2);
-                const unsigned before = same & puts & lanemask_lt();
-                const int src = before ? 31 - __clz(before) : (int)lane;
-                const uint64_t pv = shfl64(value, src);
-                if (in) {
-                    if (op == 1u) {
-                        my_out = (uint64_t)h0;
-                    } else {
-                        uint64_t cv = ~0ull;
-#pragma unroll
-                        for (int w = 0; w < 8; ++w)
-                            if (w == h0) cv = vals[w];
-                        my_out = before ? pv : cv;
-                        any_get = true;
-                        if (h0 >= 0) mark_ways |= 1u << h0;
-                    }
-                    if (h0 >= 0) {
-#pragma unroll
-                        for (int w = 0; w < 8; ++w)
-                            if (w == h0) pl[w] = max(pl[w], my_stamp);
-                        pend_ways |= 1u << h0;
-                    }
-                }
-                if (puts) {
-                    const bool last_put = ((puts >> lane) & 1u) && !(same & puts & ~lanemask_lt() & ~(1u << lane));
-                    const uint32_t wput = __reduce_or_sync(kFull, last_put ? 1u << h0 : 0u);
-#pragma unroll
-                    for (int w = 0; w < 8; ++w) {
-                        if (!((wput >> w) & 1u)) continue;
-                        const unsigned lb = __ballot_sync(kFull, last_put && h0 == w);
-                        vals[w] = shfl64(value, __ffs(lb) - 1);
-                    }
-                    dirty_kv |= wput;
-                    dirty_lru |= wput;
-                    mk.val_write |= wput;
-                    mk.lru_write |= wput;
-                    mk.ver_write = 1;
-                    ver += (uint32_t)__popc(puts);
-                }
-                if (cnt) mk.keys_read = 1;
-            } else if (!stopped) {
-                // GETs change no key or value, only stamps (by max): a stretch of
-                // GETs between two PUTs runs on all its lanes at once against
-                // the current copy; the PUTs are applied one at a time
+            if (!stopped) {
+                // The chunk is cut at every PUT of a key that is not in the set
+                // at that point (an insert, possibly evicting): such a PUT runs
+                // alone, in order.  In the stretch before it no key moves, since
+                // its PUTs all update keys already in the set in place: each GET
+                // reads the value of the last PUT to its way before it in the
+                // stretch, else the copy at the stretch's start, and each way
+                // written ends the stretch with its last PUT's value.
                 int pos = 0;
                 while (pos < cnt) {
-                    const unsigned rest = puts & ~((1u << pos) - 1u);
-                    const int np = rest ? __ffs(rest) - 1 : cnt;  // next PUT (or the end)
+                    int h0 = -1;  // this lane's key in the current copy
+#pragma unroll
+                    for (int w = 7; w >= 0; --w)
+                        if (keys[w] == key) h0 = w;
+                    const unsigned from = ~((1u << pos) - 1u);
+                    const unsigned ins = __ballot_sync(kFull, in && op == 1u && h0 < 0) & from;
+                    const int np = ins ? __ffs(ins) - 1 : cnt;  // next inserting PUT (or the end)
+                    const unsigned range = from & (np < 32 ? (1u << np) - 1u : kFull);
                     if (np > pos) {
-                        const bool get = (int)lane >= pos && (int)lane < np;
-                        int hit = -1;
+                        const bool inr = in && ((range >> lane) & 1u);
+                        const unsigned rputs = puts & range;
+                        const unsigned same = __match_any_sync(kFull, inr ? h0 : -2);
+                        const unsigned before = same & rputs & lanemask_lt();
+                        const uint64_t pv = shfl64(value, before ? 31 - __clz(before) : (int)lane);
+                        if (inr) {
+                            if (op == 1u) {
+                                my_out = (uint64_t)h0;
+                            } else {
+                                uint64_t cv = ~0ull;
 #pragma unroll
-                        for (int w = 7; w >= 0; --w)
-                            if (keys[w] == key) hit = w;
-                        if (get) {
-                            my_out = ~0ull;
-                            any_get = true;
+                                for (int w = 0; w < 8; ++w)
+                                    if (w == h0) cv = vals[w];
+                                my_out = before ? pv : cv;
+                                any_get = true;
+                                if (h0 >= 0) mark_ways |= 1u << h0;
+                            }
+                            if (h0 >= 0) {
 #pragma unroll
-                            for (int w = 0; w < 8; ++w)
-                                if (w == hit) {
-                                    my_out = vals[w];
-                                    pl[w] = max(pl[w], my_stamp);
-                                }
-                            if (hit >= 0) {
-                                pend_ways |= 1u << hit;
-                                mark_ways |= 1u << hit;
+                                for (int w = 0; w < 8; ++w)
+                                    if (w == h0) pl[w] = max(pl[w], my_stamp);
+                                pend_ways |= 1u << h0;
                             }
                         }
+                        if (rputs) {
+                            const bool last_put =
+                                ((rputs >> lane) & 1u) && !(same & rputs & ~lanemask_lt() & ~(1u << lane));
+                            const uint32_t wput = __reduce_or_sync(kFull, last_put ? 1u << h0 : 0u);
+#pragma unroll
+                            for (int w = 0; w < 8; ++w) {
+                                if (!((wput >> w) & 1u)) continue;
+                                const unsigned lb = __ballot_sync(kFull, last_put && h0 == w);
+                                vals[w] = shfl64(value, __ffs(lb) - 1);
+                            }
+                            dirty_kv |= wput;
+                            dirty_lru |= wput;
+                            mk.val_write |= wput;
+                            mk.lru_write |= wput;
+                            mk.ver_write = 1;
+                            ver += (uint32_t)__popc(rputs);
+                        }
+                        mk.keys_read = 1;
                     }
                     if (np < cnt) {
                         const uint64_t k_ = shfl64(key, np), v_ = shfl64(value, np);
                         const uint32_t stamp = (uint32_t)__shfl_sync(kFull, my_stamp, np);
-                        // a PUT that neither hits nor finds an empty way evicts by
-                        // stamp: bring the stamps up to date first (warp-uniform:
-                        // every lane holds the same copy)
-                        bool hit_or_empty = false;
+                        // a PUT that finds no empty way evicts by stamp: bring the
+                        // stamps up to date first (warp-uniform: every lane holds
+                        // the same copy)
+                        bool has_empty = false;
 #pragma unroll
-                        for (int w = 0; w < 8; ++w) hit_or_empty |= keys[w] == k_ || keys[w] == 0;
-                        if (!hit_or_empty) fold();
+                        for (int w = 0; w < 8; ++w) has_empty |= keys[w] == 0;
+                        if (!has_empty) fold();
                         const uint64_t out = cache_apply(keys, vals, lru, ver, dirty_kv, dirty_lru, k_, v_, 1u,
                                                          stamp, mk);
                         if ((int)lane == np) my_out = out;
