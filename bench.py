@@ -691,6 +691,41 @@ def run_case(name):
                           "ms_validate": st["ms_validate"], "ms_apply": st["ms_apply"],
                           "ms_merge": st["ms_merge"], "rc": st["rc"]}))
         return 0 if st["rc"] == h.HETM_OK and st["n_conflicts"] == v.n_hits_planted else 1
+    if name == "chain_links":  # cost of one link of a conflict chain, by where its two ends run
+        # 2^18 W1 updates on 4 distinct words each; every `stride`-th one also
+        # names word 0, so those form one chain of conflicting transactions whose
+        # consecutive members are `stride` ranks apart: 1 = inside a warp,
+        # 32 = one warp apart, 512 = one 512-transaction segment (CTA) apart
+        n = 1 << 18
+        log2w = 26
+        i = np.arange(n, dtype=np.uint64)
+        res = []
+        for stride in (1, 32, 512):
+            tx = np.zeros(n, dtype=wl.RMW_DTYPE)
+            a_ = ((1 << 20) + 16 + 4 * i[:, None] + np.arange(4, dtype=np.uint64)[None, :]).astype(np.uint32)
+            a_[(i % stride) == 0, 0] = 0
+            tx["addr"] = a_
+            tx["flags"] = 1
+            cfg = {"cpu_threads": 1, "max_round_tx": n, "exec_threads": 512}
+            with h.Context(1 << log2w, GRANULE, cfg) as ctx:
+                dtx = torch.from_numpy(tx.view(np.uint8)).cuda()
+                outs = (torch.empty(n, dtype=torch.int64, device="cuda"),
+                        torch.empty(n, dtype=torch.uint8, device="cuda"),
+                        torch.empty(n, dtype=torch.int32, device="cuda"))
+                ms = []
+                for r in range(4):
+                    ctx.load(torch.zeros(1 << log2w, dtype=torch.int32, device="cuda"))
+                    ctx.submit_batch(h.HETM_WL_RMW, dtx, *outs, n_tx=n)
+                    st = ctx.round(stats=True)
+                    if st["rc"] != h.HETM_OK or st["committed"] != n:
+                        return 1
+                    if r:
+                        ms.append(st["ms_exec"])
+            links = (n + stride - 1) // stride - 1
+            t = float(np.median(ms))
+            res.append({"stride": stride, "links": links, "ms_exec": t, "ns_per_link": t * 1e6 / links})
+        print(json.dumps({"case": name, "chains": res}))
+        return 0
     raise SystemExit(f"unknown case {name}")
 
 
