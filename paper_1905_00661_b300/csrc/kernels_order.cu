@@ -736,12 +736,12 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                         ok[j] = (tf[j] & kFWriter) ? c == need : c >= need;
                         if (!ok[j]) min_gap = min(min_gap, need > c ? need - c : 1u);
                     }
-                    if (__any_sync(kFull, ok[0] || ok[1] || ok[2] || ok[3])) {
-                        // acquire what the previous holders wrote before the
-                        // counters moved (cache sets), then hand the inputs on
-                        fence_gpu();
-                        any_new = true;
-                    }
+                    // No fence before handing the inputs on: every pending input
+                    // is a word whose value travels in the same 8-byte word as
+                    // its turn count (cache requests do not run here), so the
+                    // relaxed load above already holds everything the consumer
+                    // reads.
+                    if (__any_sync(kFull, ok[0] || ok[1] || ok[2] || ok[3])) any_new = true;
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         if (ok[j])
