@@ -40,6 +40,7 @@ struct Scratch {                    // device-resident counters
     unsigned int segs_done;         //   ordered-phase segments finished
     unsigned int segs_total;        //   their number + 1 (0 = not known yet)
     unsigned int exec_over;         //   nonzero once every executor kernel has finished
+    unsigned long long v0;          // optimistic executor: commit clock before the launch
 };
 
 struct RoundOut {                   // pinned copy of the round's results
@@ -359,16 +360,22 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
         }
         return HETM_OK;
     }
-    if (!per_batch) {
+    // Optimistic executor: the W1 read-only transactions of a launch run first,
+    // lock-free on the launch-start state (serialized before every update of
+    // the launch, commit key 2 * v0 + 1), so that the STM runs the updates only.
+    auto run = [&](ExecArgs e) -> int {
+        CK(cudaMemcpyAsync(&c->scr->v0, &c->scr->gv, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                           c->stream));
+        CK(launch_ro_phase(e, &c->scr->v0, c->stream_blocks, c->stream));
+        e.skip_ro = 1;
         CK(cudaMemsetAsync(&c->scr->next, 0, sizeof(unsigned long long), c->stream));
-        CK(launch_exec(exec_args(c, c->d_round, c->d_batches, c->d_prefix), c->exec_blocks,
-                       c->exec_threads, c->stream));
+        CK(launch_exec(e, c->exec_blocks, c->exec_threads, c->stream));
         return HETM_OK;
-    }
+    };
+    if (!per_batch) return run(exec_args(c, c->d_round, c->d_batches, c->d_prefix));
     for (uint32_t b = 0; b < nb; ++b) {
-        CK(cudaMemsetAsync(&c->scr->next, 0, sizeof(unsigned long long), c->stream));
-        CK(launch_exec(exec_args(c, c->d_round + 1 + b, c->d_batches + b, c->d_prefix0),
-                       c->exec_blocks, c->exec_threads, c->stream));
+        const int rc = run(exec_args(c, c->d_round + 1 + b, c->d_batches + b, c->d_prefix0));
+        if (rc != HETM_OK) return rc;
     }
     return HETM_OK;
 }

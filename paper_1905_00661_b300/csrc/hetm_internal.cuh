@@ -66,6 +66,9 @@ struct ExecArgs {
     unsigned int *segs_done, *segs_total;
     uint32_t cache_log2_sets;
     uint64_t key_base, val_base, lru_base, ver_base;
+    // optimistic executor: W1 read-only transactions already ran (lock-free,
+    // on the launch-start state, before every update of the launch)
+    uint32_t skip_ro;
 };
 
 // One transaction of the ordered phase (indexed by its rank in that phase).
@@ -170,6 +173,9 @@ __device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
 cudaError_t launch_exec(const ExecArgs &a, int blocks, int threads, cudaStream_t s);
 int exec_occupancy(int threads, int *blocks_per_sm);
 cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks, cudaStream_t s);
+// W1 read-only transactions of a launch, lock-free on the launch-start state
+// (commit key 2 * *v0 + 1: before every update of the launch)
+cudaError_t launch_ro_phase(const ExecArgs &e, unsigned long long *v0, int blocks, cudaStream_t s);
 int ordered_exec_occupancy(uint32_t seg, int *blocks_per_sm);
 
 // validation kernels: one CTA of kValThreads per SM, RS_bmp filter in shared memory

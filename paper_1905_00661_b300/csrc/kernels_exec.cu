@@ -207,6 +207,8 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
                         if (o_status) o_status[li] = kGaveUp;
                         ++n_gaveup;
                         gi = kNone;  // drawn again next iteration
+                    } else if (a.skip_ro && wl == HETM_WL_RMW && !upd) {
+                        gi = kNone;  // ran in the read-only phase
                     }
                 } else {
                     done = true;

@@ -1227,6 +1227,14 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
 
 }  // namespace
 
+cudaError_t launch_ro_phase(const ExecArgs &e, unsigned long long *v0, int blocks, cudaStream_t s) {
+    OrderArgs o{};
+    o.e = e;
+    o.v0 = v0;
+    k_ord_ro<<<blocks, 256, 0, s>>>(o);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks,
                            cudaStream_t s) {
     k_ord_count<<<stream_blocks, 256, 0, s>>>(o);
