@@ -362,7 +362,9 @@ HETM_API int hetm_round_wait(hetm_ctx *ctx, hetm_round_stats *stats);
  * to that first poll.  Ids are those hetm_gpu_submit_batch returned; the
  * context remembers the last 65,536 batches, and forgets those that
  * hetm_load discarded.  HETM_EINVAL for an unknown id or NULL pointer,
- * HETM_ECUDA if the device query failed.  Call from the controller thread. */
+ * HETM_ECUDA if the device query failed.  Call from the controller thread,
+ * and not while a hetm_server drives the context (its loop thread is then the
+ * controller). */
 #define HETM_BATCH_QUEUED 1
 #define HETM_BATCH_RUNNING 2
 #define HETM_BATCH_DONE 3
