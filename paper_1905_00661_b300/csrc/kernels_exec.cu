@@ -13,10 +13,13 @@
 //     failure, so no waiting and no deadlock), read under the locks, take a
 //     commit version v from a global clock -- one atomicAdd per warp for
 //     all its committing lanes -- write, and release the stripes at v;
-//   * read-only transactions read (lock versions, fence, values, fence,
-//     versions again) and commit when nothing changed; their commit key is
-//     2 * (newest version seen) + 1, i.e. right after the last writer they
-//     observed;
+//   * W1 read-only transactions run before this kernel, lock-free on the
+//     launch-start state, in the ordered executor's read-only phase (commit
+//     key 2 * v0 + 1: before every update of the launch; ExecArgs::skip_ro);
+//     run here instead (skip_ro = 0), a read-only transaction reads (lock
+//     versions, fence, values, fence, versions again) and commits when
+//     nothing changed, with commit key 2 * (newest version seen) + 1, i.e.
+//     right after the last writer it observed;
 //   * a cache GET that hits writes its LRU stamp: it locks that stripe at
 //     commit, takes v, then re-validates what it read (TL2 order).
 //
