@@ -149,6 +149,9 @@ struct hetm_ctx {
     bool last_gpu_survived = false;
     uint32_t gpu_losses = 0;
     std::atomic<bool> cpu_read_only{false};
+    // ordered executor: side stream of the read-only phase, and its fork/join
+    cudaStream_t ro_side = nullptr;
+    cudaEvent_t ro_fork = nullptr, ro_join = nullptr;
     // early validation: watcher stream, "stop flag reset" node of g_exec, watcher done
     bool early = false;
     cudaStream_t watch = nullptr;
@@ -347,7 +350,8 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
                 if (capturing)
                     CK(cudaEventRecordWithFlags(c->ev_watch_start, c->stream, cudaEventRecordExternal));
             }
-            CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream));
+            CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream, c->ro_side, c->ro_fork,
+                              c->ro_join));
             // stream order: set only after every kernel of the execution phase
             if (c->early) CK(cudaMemsetAsync(&c->scr->exec_over, 0xFF, sizeof(unsigned int), c->stream));
             return HETM_OK;
@@ -356,7 +360,8 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
             o.e = exec_args(c, c->d_round + 1 + b, c->d_batches + b, c->d_prefix0);
             o.e.stop = nullptr;  // no watcher runs beside per-batch launches
             o.e.segs_done = o.e.segs_total = nullptr;
-            CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream));
+            CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream, c->ro_side, c->ro_fork,
+                              c->ro_join));
         }
         return HETM_OK;
     }
@@ -519,6 +524,12 @@ void hetm_destroy(hetm_ctx *c) {
             if (b) cudaFreeHost(b);
     if (c->out) cudaFreeHost(c->out);
     if (c->rconf) cudaFreeHost(c->rconf);
+    if (c->ro_side) {
+        cudaStreamSynchronize(c->ro_side);
+        cudaStreamDestroy(c->ro_side);
+    }
+    if (c->ro_fork) cudaEventDestroy(c->ro_fork);
+    if (c->ro_join) cudaEventDestroy(c->ro_join);
     for (auto &e : c->rend)
         if (e) cudaEventDestroy(e);
     if (c->ws_host) cudaFreeHost(c->ws_host);
@@ -641,6 +652,10 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         if (cudaEventCreate(&e) != cudaSuccess) return fail(HETM_ECUDA);
     for (auto &e : c->rend)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(HETM_ECUDA);
+    if (cudaStreamCreateWithFlags(&c->ro_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ro_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ro_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(HETM_ECUDA);
     if (!host_alloc_t(&c->rconf, kRoundRing)) return fail(HETM_ENOMEM);
     std::memset(c->rconf, 0, kRoundRing * sizeof(unsigned long long));
     for (uint32_t t = 0; t < d.cpu_threads; ++t) c->tlogs.emplace_back(new ThreadLog());

@@ -172,7 +172,11 @@ __device__ __forceinline__ uint64_t splitmix_fin(uint64_t z) {
 // ----------------------------------------------------------- host launchers
 cudaError_t launch_exec(const ExecArgs &a, int blocks, int threads, cudaStream_t s);
 int exec_occupancy(int threads, int *blocks_per_sm);
-cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks, cudaStream_t s);
+// side / fork / join (all or none): the read-only phase runs on `side`, beside
+// the ordering pre-pass on `s`
+cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks, cudaStream_t s,
+                           cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
+                           cudaEvent_t join = nullptr);
 // W1 read-only transactions of a launch, lock-free on the launch-start state
 // (commit key 2 * *v0 + 1: before every update of the launch)
 cudaError_t launch_ro_phase(const ExecArgs &e, unsigned long long *v0, int blocks, cudaStream_t s);

@@ -1236,8 +1236,20 @@ cudaError_t launch_ro_phase(const ExecArgs &e, unsigned long long *v0, int block
 }
 
 cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks,
-                           cudaStream_t s) {
+                           cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
     k_ord_count<<<stream_blocks, 256, 0, s>>>(o);
+    // The read-only phase needs only the clock snapshot k_ord_count takes and
+    // the launch-start STMR^W, which nothing changes before k_seg_exec: with a
+    // side stream it runs beside the ordering pre-pass.
+    const bool beside = side && fork && join;
+    if (beside) {
+        cudaError_t e0 = cudaEventRecord(fork, s);
+        if (e0 == cudaSuccess) e0 = cudaStreamWaitEvent(side, fork, 0);
+        if (e0 != cudaSuccess) return e0;
+        k_ord_ro<<<stream_blocks, 256, 0, side>>>(o);
+        e0 = cudaEventRecord(join, side);
+        if (e0 != cudaSuccess) return e0;
+    }
     const uint32_t scan_grid = (o.cap_tx + kScanTile - 1) / kScanTile;
     cudaError_t e = device_scan<SumOp, true>(o.cnt, o.cnt, o.n_tx32, 0, scan_grid, o.scan_tot, 0, s);
     if (e != cudaSuccess) return e;
@@ -1250,7 +1262,9 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
     e = device_scan<PairMaxOp, false>(o.runs, o.runs, o.n_acc, 0, acc_grid, o.scan_tot, 0, s);
     if (e != cudaSuccess) return e;
     k_ord_acc<<<stream_blocks, 256, 0, s>>>(o);
-    k_ord_ro<<<stream_blocks, 256, 0, s>>>(o);
+    if (beside) e = cudaStreamWaitEvent(s, join, 0);
+    else k_ord_ro<<<stream_blocks, 256, 0, s>>>(o);
+    if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(o.e.next, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     switch (o.seg_log2) {
