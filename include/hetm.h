@@ -438,9 +438,121 @@ HETM_API int hetm_server_create(hetm_server **out, hetm_ctx *ctx, const hetm_ser
 HETM_API int hetm_server_submit(hetm_server *s, const hetm_request *r, uint64_t *id);
 /* Block until batch `id` completed (bounded: HETM_ETIMEOUT after 120 s). */
 HETM_API int hetm_server_wait(hetm_server *s, uint64_t id, double *latency_ms);
+/* hetm_server_wait that also gives the HETM_OUTCOME_* of the round that ran
+ * the batch (*outcome may be NULL).  After HETM_OUTCOME_GPU_ROLLED_BACK the
+ * batch's effects on the STMR were undone by the merge: its status and out
+ * buffers hold what the undone execution produced. */
+HETM_API int hetm_server_wait_outcome(hetm_server *s, uint64_t id, double *latency_ms,
+                                      uint32_t *outcome);
 HETM_API int hetm_server_get_stats(hetm_server *s, hetm_server_stats *out);
 /* Drain the queue, stop the loop thread, free the server. */
 HETM_API void hetm_server_destroy(hetm_server *s);
+
+/* ------------------------------------------------------------- dispatch */
+/* Request queues and device affinity (Sec. III-B, transaction scheduling and
+ * dispatching).  Requests are single transactions of a registered type.  A
+ * type has a transactional function (runs one request on the CPU), a
+ * transactional kernel (one of the executor's workloads, runs requests in
+ * batches on the GPU), or both.  A type with one implementation has one
+ * queue; a type with both has three: CPU_Q, GPU_Q and SHARED_Q, chosen by
+ * the affinity given at submission (none -> SHARED_Q), so that requests known
+ * to conflict can be kept on one device.
+ *   - CPU workers (cpu_workers threads) take one request at a time from the
+ *     CPU_Qs of all types in round-robin order; when every CPU_Q is empty they
+ *     steal one from a SHARED_Q (round-robin too).
+ *   - A GPU controller thread activates a type's kernel when its GPU_Q plus
+ *     SHARED_Q hold gpu_min_batch requests (the GPU steals from SHARED_Q only
+ *     what its own GPU_Q leaves of the batch), or when the oldest of them has
+ *     waited gpu_max_wait_us; a batch takes at most gpu_max_batch requests,
+ *     and at most gpu_inflight batches are outstanding.  Batches go to a
+ *     hetm_server (which fuses them into synchronization rounds) or, with no
+ *     server, to a caller-supplied batch function.
+ *   - A batch whose round ended HETM_OUTCOME_GPU_ROLLED_BACK had its effects
+ *     undone: its requests go back to the front of the queues they came from
+ *     and run again, so every request completes exactly once.
+ * The transactional function runs the request through the application's
+ * CPU TM and hands its writes to hetm_cpu_log_write (thread id = the worker
+ * index it is given).  Under HETM_POLICY_CPU_LOSES the application undoes
+ * and re-runs discarded CPU transactions itself (Sec. IV-E); the dispatcher
+ * completes a CPU request when its function returns. */
+#define HETM_AFFINITY_NONE 0
+#define HETM_AFFINITY_CPU 1
+#define HETM_AFFINITY_GPU 2
+#define HETM_DEVICE_CPU 1 /* hetm_dispatch_submit's device[] values */
+#define HETM_DEVICE_GPU 2
+
+/* Runs request `tx` on the CPU (worker index `worker`), writing out_bytes to
+ * `out` when out is not NULL.  Returns the request's status byte (0..255, 1 =
+ * committed) or a negative HETM_E* code, which fails its submission.  Called
+ * from the dispatcher's worker threads, several at a time. */
+typedef int (*hetm_cpu_tx_fn)(void *user, uint32_t worker, const void *tx, void *out);
+/* Runs n requests (packed records) on the GPU with no hetm_server attached:
+ * fills status[n] (and out, n x out_bytes, when not NULL) and *outcome with
+ * the HETM_OUTCOME_* of the round that ran them.  Returns HETM_OK or an error
+ * code, which fails every submission in the batch.  Called from the
+ * controller thread only. */
+typedef int (*hetm_gpu_batch_fn)(void *user, uint32_t workload, uint32_t word_base, const void *tx,
+                                 uint32_t n, uint8_t *status, void *out, uint32_t *outcome);
+
+typedef struct hetm_tx_type {
+    uint32_t gpu_workload;   /* HETM_WL_BANK / HETM_WL_CACHE, or 0: no kernel.
+                                HETM_WL_RMW is refused: its txid is a position
+                                in the batch, which dispatch does not fix */
+    uint32_t rec_bytes;      /* bytes of one request; the workload's record
+                                size when gpu_workload != 0                */
+    uint32_t out_bytes;      /* bytes of one result; the workload's (bank 0,
+                                cache 8) when gpu_workload != 0            */
+    uint32_t word_base;      /* the kernel's hetm_request.word_base       */
+    hetm_cpu_tx_fn cpu_fn;   /* transactional function, or NULL           */
+    void *cpu_user;
+} hetm_tx_type;
+
+typedef struct hetm_dispatch_config {
+    uint32_t cpu_workers;      /* CPU worker threads; 2                          */
+    uint32_t gpu_min_batch;    /* requests that make an activation worth it; 1024 */
+    uint32_t gpu_max_batch;    /* requests per activation; 1 << 20, clamped to the
+                                  server's max_round_tx                           */
+    uint32_t gpu_max_wait_us;  /* fewer requests activate after this wait; 2000   */
+    uint32_t gpu_inflight;     /* outstanding activations; 2                      */
+} hetm_dispatch_config;
+
+typedef struct hetm_dispatch_stats {
+    uint64_t cpu_done, gpu_done;        /* requests completed on each device      */
+    uint64_t cpu_stolen, gpu_stolen;    /* of those, taken from a SHARED_Q        */
+    uint64_t activations;               /* GPU batches completed                  */
+    uint64_t requeued;                  /* requests re-run after a rolled-back round */
+    uint64_t queued_cpu, queued_gpu, queued_shared;  /* waiting now            */
+} hetm_dispatch_stats;
+
+typedef struct hetm_dispatch hetm_dispatch;
+HETM_API int hetm_dispatch_config_default(hetm_dispatch_config *cfg);
+/* Start the worker and controller threads.  GPU batches go to `server` when
+ * it is not NULL (it must outlive the dispatcher), else to `gpu_fn`; with
+ * neither, only CPU-only types can be registered.  HETM_EINVAL for a bad
+ * config (gpu_min_batch, gpu_max_batch or gpu_inflight 0). */
+HETM_API int hetm_dispatch_create(hetm_dispatch **out, hetm_server *server, hetm_gpu_batch_fn gpu_fn,
+                                  void *gpu_user, const hetm_dispatch_config *cfg);
+/* Register a transaction type; *type gets its id (0, 1, ...).  HETM_EINVAL
+ * when it has no implementation, a record size that does not match its
+ * workload, a CPU function but no CPU workers, or a kernel but neither a
+ * server nor a batch function. */
+HETM_API int hetm_dispatch_register(hetm_dispatch *d, const hetm_tx_type *t, uint32_t *type);
+/* Queue n requests of `type` (records packed in tx, host memory) with an
+ * affinity (HETM_AFFINITY_*).  Results: status[n] (may be NULL), out (n x
+ * out_bytes, may be NULL), device[n] (HETM_DEVICE_*, may be NULL).  All
+ * buffers stay the caller's and must stay valid until hetm_dispatch_wait.
+ * Thread-safe.  HETM_EINVAL for an unknown type, an affinity naming a device
+ * the type has no implementation for, or after destroy began. */
+HETM_API int hetm_dispatch_submit(hetm_dispatch *d, uint32_t type, int affinity, const void *tx,
+                                  uint32_t n, uint8_t *status, void *out, uint8_t *device,
+                                  uint64_t *ticket);
+/* Block until every request of `ticket` completed (bounded: HETM_ETIMEOUT
+ * after 120 s); returns the first error among them, and frees the ticket.
+ * *latency_ms (may be NULL): submission to the last completion. */
+HETM_API int hetm_dispatch_wait(hetm_dispatch *d, uint64_t ticket, double *latency_ms);
+HETM_API int hetm_dispatch_get_stats(hetm_dispatch *d, hetm_dispatch_stats *out);
+/* Run every queued request, stop the threads, free the dispatcher. */
+HETM_API void hetm_dispatch_destroy(hetm_dispatch *d);
 
 /* ---------------------------------------------------- handoff latency */
 /* Committing in a fixed order serializes the writers of every word, so a

@@ -28,6 +28,8 @@ HETM_OUTCOME_CLEAN, HETM_OUTCOME_GPU_ROLLED_BACK, HETM_OUTCOME_CPU_DISCARDED = 0
 HETM_EXEC_ORDERED, HETM_EXEC_OPTIMISTIC = 0, 1
 HETM_BATCH_QUEUED, HETM_BATCH_RUNNING, HETM_BATCH_DONE = 1, 2, 3
 HETM_OUTCOME_UNKNOWN = 0xFFFFFFFF
+HETM_AFFINITY_NONE, HETM_AFFINITY_CPU, HETM_AFFINITY_GPU = 0, 1, 2
+HETM_DEVICE_CPU, HETM_DEVICE_GPU = 1, 2
 STMR_W, STMR_S, TS, RS_BMP, WS_BMP = 0, 1, 2, 3, 4
 
 LOG_DTYPE = np.dtype([("addr", "<u4"), ("value", "<i4"), ("ts", "<u4")])
@@ -84,7 +86,10 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
            "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune",
            "hetm_handoff_latency", "hetm_random_access_rate", "hetm_read_dirty",
-           "hetm_cpu_updates_allowed", "hetm_batch_poll")
+           "hetm_cpu_updates_allowed", "hetm_batch_poll", "hetm_server_wait_outcome",
+           "hetm_dispatch_config_default", "hetm_dispatch_create", "hetm_dispatch_register",
+           "hetm_dispatch_submit", "hetm_dispatch_wait", "hetm_dispatch_get_stats",
+           "hetm_dispatch_destroy")
 
 
 class hetm_tune_space(ctypes.Structure):
@@ -118,6 +123,31 @@ class hetm_server_stats(ctypes.Structure):
     _fields_ = [("rounds", _u64), ("completed", _u64), ("committed", _u64), ("refused", _u64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
                 ("span_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+#: hetm_cpu_tx_fn(user, worker, tx, out) -> status byte or negative HETM_E* code
+CPU_TX_FN = ctypes.CFUNCTYPE(_int, _vp, _u32, _vp, _vp)
+#: hetm_gpu_batch_fn(user, workload, word_base, tx, n, status, out, outcome) -> rc
+GPU_BATCH_FN = ctypes.CFUNCTYPE(_int, _vp, _u32, _u32, _vp, _u32, _vp, _vp, ctypes.POINTER(_u32))
+
+
+class hetm_tx_type(ctypes.Structure):
+    _fields_ = [("gpu_workload", _u32), ("rec_bytes", _u32), ("out_bytes", _u32),
+                ("word_base", _u32), ("cpu_fn", CPU_TX_FN), ("cpu_user", _vp)]
+
+
+class hetm_dispatch_config(ctypes.Structure):
+    _fields_ = [("cpu_workers", _u32), ("gpu_min_batch", _u32), ("gpu_max_batch", _u32),
+                ("gpu_max_wait_us", _u32), ("gpu_inflight", _u32)]
+
+
+class hetm_dispatch_stats(ctypes.Structure):
+    _fields_ = [("cpu_done", _u64), ("gpu_done", _u64), ("cpu_stolen", _u64), ("gpu_stolen", _u64),
+                ("activations", _u64), ("requeued", _u64), ("queued_cpu", _u64),
+                ("queued_gpu", _u64), ("queued_shared", _u64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -159,6 +189,14 @@ def _declare(L):
         "hetm_server_create": (_int, [P(_vp), _vp, P(hetm_server_config)]),
         "hetm_server_submit": (_int, [_vp, P(hetm_request), P(_u64)]),
         "hetm_server_wait": (_int, [_vp, _u64, P(ctypes.c_double)]),
+        "hetm_server_wait_outcome": (_int, [_vp, _u64, P(ctypes.c_double), P(_u32)]),
+        "hetm_dispatch_config_default": (_int, [P(hetm_dispatch_config)]),
+        "hetm_dispatch_create": (_int, [P(_vp), _vp, GPU_BATCH_FN, _vp, P(hetm_dispatch_config)]),
+        "hetm_dispatch_register": (_int, [_vp, P(hetm_tx_type), P(_u32)]),
+        "hetm_dispatch_submit": (_int, [_vp, _u32, _int, _vp, _u32, _vp, _vp, _vp, P(_u64)]),
+        "hetm_dispatch_wait": (_int, [_vp, _u64, P(ctypes.c_double)]),
+        "hetm_dispatch_get_stats": (_int, [_vp, P(hetm_dispatch_stats)]),
+        "hetm_dispatch_destroy": (None, [_vp]),
         "hetm_server_get_stats": (_int, [_vp, P(hetm_server_stats)]),
         "hetm_server_destroy": (None, [_vp]),
         "hetm_tune_space_default": (_int, [P(hetm_tune_space)]),
@@ -556,6 +594,109 @@ class Server:
     def close(self):
         if getattr(self, "h", None):
             _lib.hetm_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Dispatcher:
+    """Request queues with device affinity and work stealing (see include/hetm.h).
+
+    GPU batches go to ``server`` (a :class:`Server`) or, without one, to
+    ``gpu_batch(workload, word_base, tx_bytes, n, status, out) -> outcome``, a
+    Python function that fills the numpy arrays ``status`` (uint8[n]) and ``out``
+    (uint8[n * out_bytes] or None) and returns the HETM_OUTCOME_* of the round.
+    CPU functions registered with :meth:`register` are called as
+    ``cpu_fn(worker, record_bytes) -> (status, out_bytes or None)`` from the
+    dispatcher's worker threads.  This class needs no CUDA device unless a
+    server is attached."""
+
+    def __init__(self, server=None, gpu_batch=None, cpu_workers=2, gpu_min_batch=1024,
+                 gpu_max_batch=1 << 20, gpu_max_wait_us=2000, gpu_inflight=2):
+        cfg = hetm_dispatch_config()
+        _ck(_lib.hetm_dispatch_config_default(ctypes.byref(cfg)), "hetm_dispatch_config_default")
+        cfg.cpu_workers, cfg.gpu_min_batch, cfg.gpu_max_batch = cpu_workers, gpu_min_batch, gpu_max_batch
+        cfg.gpu_max_wait_us, cfg.gpu_inflight = gpu_max_wait_us, gpu_inflight
+        self._types = []   # (record bytes, out bytes, callback object)
+        self._keep = {}
+        self._gpu_cb = GPU_BATCH_FN(self._gpu_trampoline) if gpu_batch else GPU_BATCH_FN()
+        self._gpu_batch = gpu_batch
+        self.h = _vp()
+        _ck(_lib.hetm_dispatch_create(ctypes.byref(self.h), server.h if server else None,
+                                      self._gpu_cb, None, ctypes.byref(cfg)), "hetm_dispatch_create")
+
+    def _gpu_trampoline(self, user, workload, word_base, tx, n, status, out, outcome):
+        try:
+            rb = {HETM_WL_BANK: 12, HETM_WL_CACHE: 24}[workload]
+            ob = 8 if workload == HETM_WL_CACHE else 0
+            txb = np.frombuffer(ctypes.string_at(tx, n * rb), np.uint8)
+            st = np.zeros(n, np.uint8)
+            o = np.zeros(n * ob, np.uint8) if ob and out else None
+            outcome[0] = int(self._gpu_batch(workload, word_base, txb, n, st, o))
+            ctypes.memmove(status, st.ctypes.data, n)
+            if o is not None:
+                ctypes.memmove(out, o.ctypes.data, o.nbytes)
+            return HETM_OK
+        except Exception:  # reported to the submissions of the batch
+            return HETM_EINVAL
+
+    def register(self, rec_bytes, gpu_workload=0, out_bytes=0, word_base=0, cpu_fn=None):
+        """Register a transaction type; returns its id."""
+        cb = CPU_TX_FN()
+        if cpu_fn is not None:
+            def tramp(user, worker, tx, out, _f=cpu_fn, _rb=rec_bytes, _ob=out_bytes):
+                try:
+                    st, o = _f(worker, ctypes.string_at(tx, _rb))
+                    if out and _ob and o is not None:
+                        ctypes.memmove(out, bytes(o)[:_ob], _ob)
+                    return int(st)
+                except Exception:
+                    return HETM_EINVAL
+            cb = CPU_TX_FN(tramp)
+        t = hetm_tx_type(gpu_workload, rec_bytes, out_bytes, word_base, cb, None)
+        tid = _u32()
+        _ck(_lib.hetm_dispatch_register(self.h, ctypes.byref(t), ctypes.byref(tid)),
+            "hetm_dispatch_register")
+        self._types.append((rec_bytes, out_bytes, cb))
+        return tid.value
+
+    def submit(self, type_id, records, affinity=HETM_AFFINITY_NONE):
+        """Queue the requests in ``records`` (a numpy record array); returns
+        (ticket, status uint8[n], out uint8[n * out_bytes] or None, device uint8[n]),
+        the result arrays being filled by the time :meth:`wait` returns."""
+        rec = np.ascontiguousarray(records)
+        rb, ob, _ = self._types[type_id]
+        assert rec.dtype.itemsize == rb
+        n = len(rec)
+        status = np.zeros(n, np.uint8)
+        device = np.zeros(n, np.uint8)
+        out = np.zeros(n * ob, np.uint8) if ob else None
+        tk = _u64()
+        _ck(_lib.hetm_dispatch_submit(self.h, type_id, affinity, rec.ctypes.data, n,
+                                      status.ctypes.data, _ptr(out), device.ctypes.data,
+                                      ctypes.byref(tk)), "hetm_dispatch_submit")
+        self._keep[tk.value] = rec
+        return tk.value, status, out, device
+
+    def wait(self, ticket):
+        lat = ctypes.c_double()
+        rc = _lib.hetm_dispatch_wait(self.h, ticket, ctypes.byref(lat))
+        self._keep.pop(ticket, None)
+        _ck(rc, "hetm_dispatch_wait")
+        return lat.value
+
+    def stats(self):
+        st = hetm_dispatch_stats()
+        _ck(_lib.hetm_dispatch_get_stats(self.h, ctypes.byref(st)), "hetm_dispatch_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.hetm_dispatch_destroy(self.h)
             self.h = None
 
     def __enter__(self):

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "hetm.h"
+#include "hetm_internal.cuh"
 
 namespace {
 
@@ -53,6 +54,7 @@ struct Req {
     int rc = HETM_OK;
     double latency_ms = 0;
     uint32_t committed = 0;
+    uint32_t outcome = 0;  // HETM_OUTCOME_* of its round
 };
 
 }  // namespace
@@ -188,6 +190,7 @@ void complete_round(hetm_server *s, std::vector<Req *> &group, int rc) {
     for (Req *q : group) {
         q->committed = (uint32_t)std::min<uint64_t>(left, q->r.n_tx);
         left -= q->committed;
+        q->outcome = st.outcome;
     }
     {
         std::lock_guard<std::mutex> g(s->mu);
@@ -330,6 +333,10 @@ int hetm_server_submit(hetm_server *s, const hetm_request *r, uint64_t *id) {
 }
 
 int hetm_server_wait(hetm_server *s, uint64_t id, double *latency_ms) {
+    return hetm_server_wait_outcome(s, id, latency_ms, nullptr);
+}
+
+int hetm_server_wait_outcome(hetm_server *s, uint64_t id, double *latency_ms, uint32_t *outcome) {
     if (!s) return HETM_EINVAL;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->all.find(id);
@@ -338,6 +345,7 @@ int hetm_server_wait(hetm_server *s, uint64_t id, double *latency_ms) {
     if (!s->cv_done.wait_for(lk, std::chrono::seconds(120), [&] { return q->done != 0; }))
         return HETM_ETIMEOUT;
     if (latency_ms) *latency_ms = q->latency_ms;
+    if (outcome) *outcome = q->outcome;
     const int rc = q->rc;
     s->all.erase(it);
     delete q;
@@ -382,3 +390,7 @@ void hetm_server_destroy(hetm_server *s) {
 }
 
 }  // extern "C"
+
+namespace hetm {
+uint64_t server_max_round_tx(const hetm_server *s) { return s->cfg.max_round_tx; }
+}  // namespace hetm
