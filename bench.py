@@ -437,6 +437,50 @@ def bench_contention(torch, h, inputs, tuned, probs=(0.0, 0.25, 0.5, 0.75, 1.0),
     return out
 
 
+def bench_host_merge(torch, h, inputs, tuned, rounds=6):
+    """The host side of the merge each round (Sec. IV-C merge phase): the GPU-dirty
+    chunks go to a pinned 2^28-word host replica.  Synchronously after each round
+    (``read_dirty``) or double-buffered (Sec. IV-D, ``read_dirty_async``): the copy
+    of round r overlaps the execution phase of round r+1, which reads and writes
+    STMR^W only.  Host wall time per round, both ways."""
+    init, batches, logs = inputs
+    dev_tx = torch.from_numpy(batches[0].view(np.uint8)).cuda()
+    o = torch.empty(N_TX, dtype=torch.int64, device="cuda")
+    st_ = torch.empty(N_TX, dtype=torch.uint8, device="cuda")
+    res = torch.empty(N_TX, dtype=torch.int32, device="cuda")
+    dlogs = [torch.from_numpy(log_for_round(logs, r).view(np.uint8)).cuda() for r in range(rounds + 1)]
+    host = torch.from_numpy(init.copy()).pin_memory()
+    cfg = dict({"cpu_threads": 1, "log_capacity": 1 << 12}, **tuned["config"])
+    out = {"rounds": rounds, "replica_bytes": init.nbytes}
+    with h.Context(1 << LOG2W, tuned["granule_bytes"], cfg) as ctx:
+        for mode in ("sync", "async"):
+            ctx.load(init)
+            host.copy_(torch.from_numpy(init))
+            nbytes = 0
+            for r in range(rounds + 1):
+                if r == 1:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                ctx.log_attach(dlogs[r], N_LOG)
+                ctx.submit_batch(h.HETM_WL_RMW, dev_tx, o, st_, res, n_tx=N_TX,
+                                 txid_base=(r * N_TX) & 0xFFFFFFFF)
+                st = ctx.round(stats=True)
+                assert st["rc"] == h.HETM_OK and not st["conflict"]
+                if mode == "sync":
+                    _, b = ctx.read_dirty(host.numpy())
+                else:
+                    _, b = ctx.read_dirty_async(host)
+                nbytes += b if r else 0
+            ctx.read_dirty_wait()
+            dt = time.perf_counter() - t0
+            out[mode + "_ms_per_round"] = 1e3 * dt / rounds
+            out["dirty_bytes_per_round"] = nbytes / rounds
+            half = (1 << LOG2W) // 2   # the GPU's half: the replica must equal W there
+            w = ctx.read_stmr(h.STMR_W, 0, half)
+            out[mode + "_replica_matches"] = bool(np.array_equal(host.numpy()[:half], w))
+    return out
+
+
 def cpu_mt_sync(v):
     """The timed multithreaded CPU baseline (std::thread, every host core) of
     validation + apply on the same 16.8M-tuple log and 2^28-word STMR."""
@@ -813,6 +857,7 @@ def main():
     handoff_g, handoff_s = h.handoff_latency(20000)
     ra = h.random_access_rate(LOG2W, 1 << 28)
     contention = bench_contention(torch, h, inputs, res["tuned"])
+    host_merge = bench_host_merge(torch, h, inputs, res["tuned"])
     w1 = [bench_w1_uniform(torch, h, inputs[0], f) for f in (0.1, 1.0)]
     for x in w1:
         x["random_roofline"] = random_bound({"reads": x.pop("word_reads"),
@@ -871,6 +916,7 @@ def main():
                       ra, exec_ms)},
         "random_access_per_s": {"read": ra[0], "write": ra[1], "array_words": 1 << LOG2W},
         "contention": contention,
+        "host_merge": host_merge,
         "w1_uniform": w1,
         "cache": cache,
         "validation": {"kernel": "k_validate_direct", "ms": val["ms"], "gbs": val["gbs"],

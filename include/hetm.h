@@ -390,6 +390,20 @@ HETM_API int hetm_batch_poll(hetm_ctx *ctx, uint64_t batch_id, hetm_batch_result
  * *n_chunks / *n_bytes (may be NULL) get what was copied.  Synchronous. */
 HETM_API int hetm_read_dirty(hetm_ctx *ctx, int32_t *host_stmr, uint64_t *n_chunks, uint64_t *n_bytes);
 
+/* Double-buffered form of hetm_read_dirty (Sec. IV-D: the shadow STMR^S lets
+ * the copy to the host overlap the next execution phase, which reads and
+ * writes STMR^W only).  Queues the same copies on a side stream and returns;
+ * the next call that writes STMR^S (the synchronization phase of
+ * hetm_round, hetm_validate, hetm_merge, hetm_load) waits for them on the
+ * device, so they see the last round's STMR^S.  host_stmr must be pinned
+ * (cudaHostAlloc / cudaHostRegister) for the copies to be asynchronous, and
+ * must not be read before hetm_read_dirty_wait returns.  Same precondition
+ * as hetm_read_dirty: the last round's stats were collected. */
+HETM_API int hetm_read_dirty_async(hetm_ctx *ctx, int32_t *host_stmr, uint64_t *n_chunks,
+                                   uint64_t *n_bytes);
+/* Block until the copies of the last hetm_read_dirty_async are in host memory. */
+HETM_API int hetm_read_dirty_wait(hetm_ctx *ctx);
+
 /* 1 when CPU update transactions may run in the current execution phase; 0
  * while the anti-starvation rule holds the CPU to read-only transactions
  * (starve_limit). */

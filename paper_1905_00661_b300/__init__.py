@@ -89,7 +89,7 @@ SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", 
            "hetm_cpu_updates_allowed", "hetm_batch_poll", "hetm_server_wait_outcome",
            "hetm_dispatch_config_default", "hetm_dispatch_create", "hetm_dispatch_register",
            "hetm_dispatch_submit", "hetm_dispatch_wait", "hetm_dispatch_get_stats",
-           "hetm_dispatch_destroy")
+           "hetm_dispatch_destroy", "hetm_read_dirty_async", "hetm_read_dirty_wait")
 
 
 class hetm_tune_space(ctypes.Structure):
@@ -203,6 +203,8 @@ def _declare(L):
         "hetm_handoff_latency": (_int, [_u32, P(ctypes.c_double), P(ctypes.c_double)]),
         "hetm_random_access_rate": (_int, [_u32, _u64, P(ctypes.c_double), P(ctypes.c_double)]),
         "hetm_read_dirty": (_int, [_vp, _vp, P(_u64), P(_u64)]),
+        "hetm_read_dirty_async": (_int, [_vp, _vp, P(_u64), P(_u64)]),
+        "hetm_read_dirty_wait": (_int, [_vp]),
         "hetm_cpu_updates_allowed": (_int, [_vp]),
         "hetm_autotune": (_int, [_u64, _vp, P(hetm_batch), _u32, _vp, _u64, P(hetm_config),
                                  P(hetm_tune_space), P(hetm_config), P(_u32), P(hetm_tune_trial),
@@ -507,6 +509,28 @@ class Context:
         _ck(_lib.hetm_read_dirty(self.h, host_stmr.ctypes.data, ctypes.byref(c), ctypes.byref(b)),
             "hetm_read_dirty")
         return c.value, b.value
+
+    def read_dirty_async(self, host_stmr):
+        """Double-buffered read_dirty: queue the copies into ``host_stmr`` (a pinned
+        int32 torch CPU tensor of stmr_words, or a numpy array -- then the copies
+        are synchronous) and return (chunks, bytes) at once; the next write of
+        STMR^S waits for them on the device.  Read the replica after
+        :meth:`read_dirty_wait`."""
+        if isinstance(host_stmr, np.ndarray):
+            assert host_stmr.dtype == np.int32 and host_stmr.flags["C_CONTIGUOUS"]
+            size, addr = host_stmr.size, host_stmr.ctypes.data
+        else:
+            assert host_stmr.dtype == self.torch.int32 and not host_stmr.is_cuda
+            assert host_stmr.is_contiguous()
+            size, addr = host_stmr.numel(), host_stmr.data_ptr()
+        assert size == self.n_words
+        c, b = _u64(), _u64()
+        _ck(_lib.hetm_read_dirty_async(self.h, addr, ctypes.byref(c), ctypes.byref(b)),
+            "hetm_read_dirty_async")
+        return c.value, b.value
+
+    def read_dirty_wait(self):
+        _ck(_lib.hetm_read_dirty_wait(self.h), "hetm_read_dirty_wait")
 
     def cpu_updates_allowed(self) -> bool:
         return bool(_lib.hetm_cpu_updates_allowed(self.h))

@@ -149,6 +149,12 @@ struct hetm_ctx {
     bool last_gpu_survived = false;
     uint32_t gpu_losses = 0;
     std::atomic<bool> cpu_read_only{false};
+    // double-buffered merge to the host (hetm_read_dirty_async): its stream,
+    // "round ended" / "copies done" events, and whether the next write of
+    // STMR^S must still wait for the copies
+    cudaStream_t d2h = nullptr;
+    cudaEvent_t ev_d2h_from = nullptr, ev_d2h_done = nullptr;
+    bool d2h_pending = false, d2h_recorded = false;
     // ordered executor: side stream of the read-only phase, and its fork/join
     cudaStream_t ro_side = nullptr;
     cudaEvent_t ro_fork = nullptr, ro_join = nullptr;
@@ -180,6 +186,14 @@ struct hetm_ctx {
     } while (0)
 
 namespace {
+
+// Order the context stream after the host copies of hetm_read_dirty_async
+// still reading STMR^S; every write of STMR^S (apply, merge, load) comes after.
+cudaError_t after_host_copies(hetm_ctx *c) {
+    if (!c->d2h_pending) return cudaSuccess;
+    c->d2h_pending = false;
+    return cudaStreamWaitEvent(c->stream, c->ev_d2h_done, 0);
+}
 
 void *dev_alloc(hetm_ctx *c, size_t bytes) {
     void *p = nullptr;
@@ -528,6 +542,12 @@ void hetm_destroy(hetm_ctx *c) {
         cudaStreamSynchronize(c->ro_side);
         cudaStreamDestroy(c->ro_side);
     }
+    if (c->d2h) {
+        cudaStreamSynchronize(c->d2h);
+        cudaStreamDestroy(c->d2h);
+    }
+    if (c->ev_d2h_from) cudaEventDestroy(c->ev_d2h_from);
+    if (c->ev_d2h_done) cudaEventDestroy(c->ev_d2h_done);
     if (c->ro_fork) cudaEventDestroy(c->ro_fork);
     if (c->ro_join) cudaEventDestroy(c->ro_join);
     for (auto &e : c->rend)
@@ -652,6 +672,10 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         if (cudaEventCreate(&e) != cudaSuccess) return fail(HETM_ECUDA);
     for (auto &e : c->rend)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(HETM_ECUDA);
+    if (cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_d2h_from, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_d2h_done, cudaEventDisableTiming) != cudaSuccess)
+        return fail(HETM_ECUDA);
     if (cudaStreamCreateWithFlags(&c->ro_side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ro_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ro_join, cudaEventDisableTiming) != cudaSuccess)
@@ -697,6 +721,7 @@ int hetm_load(hetm_ctx *c, const int32_t *src, uint64_t n) {
     if (!c || !src || n != c->n_words) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->ship));
+    CK(after_host_copies(c));
     CK(cudaMemcpyAsync(c->W, src, n * 4, cudaMemcpyDefault, c->stream));
     CK(cudaMemcpyAsync(c->S, c->W, n * 4, cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemsetAsync(c->TS, 0, n * 4, c->stream));
@@ -897,6 +922,7 @@ int hetm_validate(hetm_ctx *c, uint64_t *n_conflicts, uint32_t *dev_flag_bits) {
     keep.swap(c->pending);
     if (rc != HETM_OK) return rc;
     CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
+    CK(after_host_copies(c));
     CK(cudaMemsetAsync(&c->scr->conflicts, 0, sizeof(unsigned long long), c->stream));
     rc = enqueue_validate_apply(c, dev_flag_bits, nullptr);
     if (rc != HETM_OK) return rc;
@@ -930,6 +956,7 @@ int hetm_validate_only(hetm_ctx *c, const hetm_log_entry *dev_log, uint64_t n,
 int hetm_merge(hetm_ctx *c, int conflict) {
     if (!c || conflict < -1 || conflict > 1) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
+    CK(after_host_copies(c));
     CK(cudaMemsetAsync(&c->scr->dirty, 0, sizeof(unsigned long long), c->stream));
     CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, conflict,
                     &c->scr->dirty, c->stream_blocks, c->stream));
@@ -985,6 +1012,7 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
         CK(cudaStreamWaitEvent(c->stream, c->ev_watch_done, 0));
     }
     CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
+    CK(after_host_copies(c));  // the execution phase above overlapped them
     CK(cudaGraphLaunch(c->g_sync, c->stream));
     CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
     if (c->exec_round) {
@@ -1026,6 +1054,45 @@ int hetm_read_dirty(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_
     }
     if (n_chunks) *n_chunks = chunks;
     if (n_bytes) *n_bytes = bytes;
+    return HETM_OK;
+}
+
+int hetm_read_dirty_async(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_bytes) {
+    if (!c || !host) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));  // the dirty map and outcome of the last round
+    uint64_t chunks = 0, bytes = 0;
+    if (c->last_gpu_survived) {
+        CK(cudaEventRecord(c->ev_d2h_from, c->stream));
+        CK(cudaStreamWaitEvent(c->d2h, c->ev_d2h_from, 0));
+        const uint64_t wpc = 1ull << c->cshift;
+        const uint64_t n_chunk = (c->n_words + wpc - 1) / wpc;
+        uint64_t ch = 0;
+        while (ch < n_chunk) {
+            if (!((c->ws_host[ch >> 5] >> (ch & 31)) & 1u)) {
+                ++ch;
+                continue;
+            }
+            uint64_t end = ch + 1;
+            while (end < n_chunk && ((c->ws_host[end >> 5] >> (end & 31)) & 1u)) ++end;
+            const uint64_t w0 = ch * wpc, w1 = std::min<uint64_t>(end * wpc, c->n_words);
+            CK(cudaMemcpyAsync(host + w0, c->S + w0, (w1 - w0) * 4, cudaMemcpyDeviceToHost, c->d2h));
+            chunks += end - ch;
+            bytes += (w1 - w0) * 4;
+            ch = end;
+        }
+        CK(cudaEventRecord(c->ev_d2h_done, c->d2h));
+        c->d2h_pending = c->d2h_recorded = true;
+    }
+    if (n_chunks) *n_chunks = chunks;
+    if (n_bytes) *n_bytes = bytes;
+    return HETM_OK;
+}
+
+int hetm_read_dirty_wait(hetm_ctx *c) {
+    if (!c) return HETM_EINVAL;
+    CK(cudaSetDevice(c->device));
+    if (c->d2h_recorded) CK(cudaEventSynchronize(c->ev_d2h_done));
     return HETM_OK;
 }
 
