@@ -1009,6 +1009,21 @@ __global__ void __launch_bounds__(256) k_cache_gather(OrderArgs o) {
 // One warp per cache run (see cache_apply); the next 32 staged requests are
 // loaded while the current ones are applied.  Early validation's stop flag
 // leaves runs not yet started as not run.
+// One staged cache request of a run (a lane's slot of a 32-request chunk).
+struct CacheStage {
+    uint64_t key, value;
+    uint32_t meta, li, u, res;
+};
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
 __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
     const ExecArgs &a = o.e;
     const uint32_t n_runs = *o.n_cache_runs;
@@ -1018,6 +1033,7 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
     const unsigned lane = threadIdx.x & 31u;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    __shared__ CacheStage stage_ring[8][2][32];  // per warp: the chunk in use and the next one
     unsigned long long n_commit = 0;
     for (uint32_t ri = warp; ri < n_runs; ri += n_warps) {
         const uint32_t head = o.cache_heads[ri];
@@ -1047,18 +1063,25 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
         }
         uint32_t ver = (uint32_t)a.W[res], ver0 = ver, dirty_kv = 0, dirty_lru = 0;
         CacheMarks mk{};
-        // staged request of lane `lane` in the chunk at `base`
-        auto stage = [&](uint32_t base, bool &in, uint64_t &key, uint64_t &value, uint32_t &meta,
-                         uint32_t &li, uint32_t &u) {
-            const uint32_t j = base + lane;
-            in = j < n_acc && o.keys0[j] == res;  // the run is contiguous: a prefix of lanes
-            if (in) {
-                key = o.packed[j];
-                value = o.runs[j];
-                meta = o.keys1[j];
-                li = o.vals1[j];
-                u = o.vals0[j];
+        // Chunk c of the run (its 32 requests, one per lane) is copied into
+        // this warp's shared-memory slot c & 1 by cp.async while chunk c - 1
+        // is applied: the six copies of a lane issue at once and hold no
+        // registers, where register staging had to wait for the access-list
+        // key (is the request in the run?) before loading the rest.  Each
+        // lane copies and reads only its own slot entry.
+        CacheStage(&ring)[2][32] = stage_ring[threadIdx.x >> 5];
+        auto issue = [&](uint32_t c) {
+            const uint32_t j = head + 32u * c + lane;
+            CacheStage &e = ring[c & 1u][lane];
+            if (j < n_acc) {
+                cp_async8(&e.key, o.packed + j);
+                cp_async8(&e.value, o.runs + j);
+                cp_async4(&e.meta, o.keys1 + j);
+                cp_async4(&e.li, o.vals1 + j);
+                cp_async4(&e.u, o.vals0 + j);
+                cp_async4(&e.res, o.keys0 + j);
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");
         };
         // GPU stamps only grow, and stamps grow with the rank, so a way's
         // stamp is the largest stamp of any access to it.  A GET therefore
@@ -1076,14 +1099,25 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
                 if ((wa >> w) & 1u) lru[w] = max(lru[w], __reduce_max_sync(kFull, pl[w]));
             pend_ways = 0;
         };
-        bool in = false, in_n = false;
-        uint64_t key = 0, value = 0, key_n = 0, value_n = 0;
-        uint32_t meta = 0, li = 0, u = 0, meta_n = 0, li_n = 0, u_n = 0;
-        stage(head, in, key, value, meta, li, u);
-        for (uint32_t base = head;; base += 32) {
+        bool in = false;
+        uint64_t key = 0, value = 0;
+        uint32_t meta = 0, li = 0, u = 0;
+        issue(0);
+        for (uint32_t c = 0;; ++c) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            {
+                const uint32_t j = head + 32u * c + lane;
+                const CacheStage &e = ring[c & 1u][lane];
+                in = j < n_acc && e.res == res;  // the run is contiguous: a prefix of lanes
+                key = e.key;
+                value = e.value;
+                meta = e.meta;
+                li = e.li;
+                u = e.u;
+            }
             const unsigned m = __ballot_sync(kFull, in);
             const int cnt = __popc(m);
-            if (cnt == 32) stage(base + 32, in_n, key_n, value_n, meta_n, li_n, u_n);
+            if (cnt == 32) issue(c + 1);  // the run goes on: copy its next chunk
             const uint32_t op = meta & 1u;
             const DevBatch *d = in ? a.batches + (meta >> 1) : nullptr;
             uint64_t my_out = 0;
@@ -1179,13 +1213,8 @@ __global__ void __launch_bounds__(256) k_cache_runs(OrderArgs o) {
             }
             if (!stopped) n_commit += in ? 1u : 0u;
             if (cnt < 32) break;
-            in = in_n;
-            key = key_n;
-            value = value_n;
-            meta = meta_n;
-            li = li_n;
-            u = u_n;
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
         if (stopped) continue;
         fold();
         {
