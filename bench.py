@@ -700,6 +700,24 @@ def run_case(name):
         print(json.dumps({"case": name, "committed": st["committed"], "ms_exec": st["ms_exec"],
                           "rc": st["rc"]}))
         return st["rc"]
+    if name == "w1_uniform":  # W1, 4 uniform words, 10% updates, optimistic executor, 2^28 words
+        init = wl.init_stmr(SEED, 1 << LOG2W)
+        tx = wl.rmw_batch(seed=SEED, batch=7, n_tx=N_TX, log2_words=LOG2W, uniform=True,
+                          update_frac=0.1)
+        cfg = {"cpu_threads": 1, "exec_mode": 1, "exec_threads": 256, "lock_log2": 24}
+        with h.Context(1 << LOG2W, GRANULE, cfg) as ctx:
+            ctx.load(init)
+            dtx = torch.from_numpy(tx.view(np.uint8)).cuda()
+            o = torch.empty(len(tx), dtype=torch.int64, device="cuda")
+            st_ = torch.empty(len(tx), dtype=torch.uint8, device="cuda")
+            out = torch.empty(len(tx), dtype=torch.int32, device="cuda")
+            ms = []
+            for r in range(3):
+                ctx.submit_batch(h.HETM_WL_RMW, dtx, o, st_, out, txid_base=r * N_TX, n_tx=len(tx))
+                st = ctx.round(stats=True)
+                ms.append(st["ms_exec"])
+        print(json.dumps({"case": name, "committed": st["committed"], "ms_exec": ms, "rc": st["rc"]}))
+        return st["rc"]
     if name == "validate_small":  # validation-at-scale log (16M tuples) on a 2^27-word STMR
         v = wl.validation_round(seed=1, log2_words=27, granule_bytes=32, with_init=False)
         with h.Context(1 << 27, 32, {"log_capacity": 1 << 12, "exec_mode": 1}) as ctx:

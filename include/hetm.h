@@ -145,7 +145,10 @@ typedef struct hetm_config {
                                   the execution phase (the round is lost to the
                                   CPU anyway under GPU-loses).  Ordered mode,
                                   fused rounds only; 0                        */
-    uint64_t max_round_tx;     /* ordered mode: transactions per execution phase; 1<<22 */
+    uint64_t max_round_tx;     /* ordered mode: transactions per execution phase; 1<<22.
+                                  Optimistic mode: launches up to this size
+                                  hand the STM a list of the transactions
+                                  their read-only phase left (4 B per tx) */
     /* Optional device allocator (e.g. a framework's caching allocator);
      * NULL = cudaMalloc/cudaFree.  Called only from hetm_init/hetm_destroy. */
     void *(*dev_alloc)(size_t bytes, void *user);

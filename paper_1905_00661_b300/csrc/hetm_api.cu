@@ -41,6 +41,7 @@ struct Scratch {                    // device-resident counters
     unsigned int segs_total;        //   their number + 1 (0 = not known yet)
     unsigned int exec_over;         //   nonzero once every executor kernel has finished
     unsigned long long v0;          // optimistic executor: commit clock before the launch
+    unsigned long long rest_n;      //   indices the read-only phase left to the STM
 };
 
 struct RoundOut {                   // pinned copy of the round's results
@@ -164,6 +165,7 @@ struct hetm_ctx {
     cudaEvent_t ev_watch_start = nullptr, ev_watch_done = nullptr;
 
     OrderArgs ord{};               // ordered-executor scratch (exec_mode ORDERED)
+    uint32_t *rest = nullptr;      // optimistic executor: indices left by the read-only phase
     int ord_blocks = 0;
     int exec_blocks = 0, exec_threads = 256, stream_blocks = 0;
     unsigned long long prev_counters[3] = {0, 0, 0};
@@ -385,6 +387,10 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
     auto run = [&](ExecArgs e) -> int {
         CK(cudaMemcpyAsync(&c->scr->v0, &c->scr->gv, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
                            c->stream));
+        e.rest = c->rest;
+        e.rest_n = &c->scr->rest_n;
+        e.rest_cap = c->rest ? c->cfg.max_round_tx : 0;
+        if (c->rest) CK(cudaMemsetAsync(&c->scr->rest_n, 0, sizeof(unsigned long long), c->stream));
         CK(launch_ro_phase(e, &c->scr->v0, c->stream_blocks, c->stream));
         e.skip_ro = 1;
         CK(cudaMemsetAsync(&c->scr->next, 0, sizeof(unsigned long long), c->stream));
@@ -629,6 +635,11 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         !dev_alloc_t(c, &c->d_batches, nb) || !dev_alloc_t(c, &c->d_prefix, nb + 1) ||
         !dev_alloc_t(c, &c->d_prefix0, 2) || !dev_alloc_t(c, &c->dlog[0], d.log_capacity) ||
         !dev_alloc_t(c, &c->dlog[1], d.log_capacity))
+        return fail(HETM_ENOMEM);
+    // optimistic executor: the list of indices its read-only phase leaves to
+    // the STM (rounds above max_round_tx transactions go unlisted)
+    if (d.exec_mode == HETM_EXEC_OPTIMISTIC && d.max_round_tx && d.max_round_tx <= (1ull << 32) &&
+        !dev_alloc_t(c, &c->rest, d.max_round_tx))
         return fail(HETM_ENOMEM);
     if (d.exec_mode == HETM_EXEC_ORDERED) {
         OrderArgs &o = c->ord;

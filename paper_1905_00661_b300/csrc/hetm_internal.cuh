@@ -69,6 +69,13 @@ struct ExecArgs {
     // optimistic executor: W1 read-only transactions already ran (lock-free,
     // on the launch-start state, before every update of the launch)
     uint32_t skip_ro;
+    // optimistic executor (null otherwise): the read-only phase lists the
+    // launch indices it did not run (rest[0 .. *rest_n)), so that the STM
+    // draws only those; a launch of more than rest_cap transactions is not
+    // listed and the STM draws every index
+    uint32_t *rest;
+    unsigned long long *rest_n;
+    uint64_t rest_cap;
 };
 
 // One transaction of the ordered phase (indexed by its rank in that phase).

@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
     const Exec x{a};
     const uint32_t n_batches = a.rp->n_batches;
     const uint64_t total = a.rp->total_tx;
+    // after the read-only phase: draw only the indices it left (when listed)
+    const bool listed = a.skip_ro && a.rest && total <= a.rest_cap;
+    const uint64_t n_draw = listed ? *a.rest_n : total;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long mine =
         ((unsigned long long)(blockIdx.x * blockDim.x + threadIdx.x + 1) << 1) | 1ull;
@@ -166,8 +169,8 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
             base = __shfl_sync(kFull, base, leader);
             if (need) {
                 const uint64_t my = base + __popc(nm & lanemask_lt());
-                if (my < total) {
-                    gi = my;
+                if (my < n_draw) {
+                    gi = listed ? a.rest[my] : my;
                     attempts = 0;
                     sit = 0;
                     const int b = binsearch(a.prefix, n_batches, gi);

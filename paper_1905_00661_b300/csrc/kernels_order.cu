@@ -483,17 +483,16 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
     const uint64_t total = a.rp->total_tx;
     const unsigned long long key = 2ull * (*o.v0) + 1;
     const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    const bool listing = a.rest && total <= a.rest_cap;
     unsigned long long n_commit = 0;
-    // loop bound rounded up to whole warps so that the warp reduction below is convergent
-    const uint64_t span = (total + 31) & ~31ull;
-    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < span; u += stride) {
-        if (u >= total) continue;
+    // runs launch index u if it is a W1 read-only transaction; true if it ran
+    auto run_ro = [&](uint64_t u) -> bool {
         const int b = find_batch(a.prefix, a.rp->n_batches, u);
         const DevBatch &d = a.batches[b];
-        if (d.workload != HETM_WL_RMW) continue;
+        if (d.workload != HETM_WL_RMW) return false;
         const uint32_t li = (uint32_t)(u - a.prefix[b]);
         const hetm_rmw_tx *x = static_cast<const hetm_rmw_tx *>(d.tx) + li;
-        if (x->flags & 1u) continue;
+        if (x->flags & 1u) return false;
         uint32_t ad[4];
         bool ok = true;
 #pragma unroll
@@ -501,7 +500,7 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
             ad[k] = x->addr[k];
             ok &= ad[k] < a.n_words;
         }
-        if (!ok) continue;  // reported by k_ord_count
+        if (!ok) return false;  // reported by k_ord_count or the STM
         int32_t s = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) s += a.W[ad[k]];
@@ -510,7 +509,21 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
         if (d.order) d.order[li] = key;
         if (d.out) static_cast<int32_t *>(d.out)[li] = s;
         if (d.status) d.status[li] = kCommitted;
-        ++n_commit;
+        return true;
+    };
+    // loop bound rounded up to whole warps so that the warp collectives below are convergent
+    const uint64_t span = (total + 31) & ~31ull;
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < span; u += stride) {
+        const bool ran = u < total && run_ro(u);
+        n_commit += ran ? 1u : 0u;
+        if (listing) {  // the indices left to the STM, appended warp by warp
+            const bool left = u < total && !ran;
+            const unsigned m = __ballot_sync(kFull, left);
+            unsigned long long base = 0;
+            if (m && (threadIdx.x & 31u) == 0) base = atomicAdd(a.rest_n, (unsigned long long)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (left) a.rest[base + __popc(m & lanemask_lt())] = (uint32_t)u;
+        }
     }
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1) n_commit += __shfl_xor_sync(kFull, n_commit, w);

@@ -194,6 +194,28 @@ def test_rmw_uneven_batches_one_launch_and_per_batch(hetm, torch, mode):
             _exec_and_check_replay(ctx, h, torch, start, batches, G, 64)
 
 
+def test_optimistic_launches_above_the_listing_capacity(hetm, torch):
+    """Optimistic executor with max_round_tx = 1000: a launch of at most 1000
+    transactions hands the STM the list of updates its read-only phase left, a
+    larger one is not listed and the STM draws every index.  Fused (one
+    unlisted launch) and per batch (listed and unlisted launches): replay parity."""
+    h = hetm
+    log2w, G = 15, 4
+    start = wl.init_words(19, 0, 1 << log2w)
+    sizes = [1000, 33, 4097, 999, 1001]
+    txs = [wl.rmw_batch(seed=19, batch=i, n_tx=n, log2_words=log2w, update_frac=0.3)
+           for i, n in enumerate(sizes)]
+    for per_batch in (False, True):
+        with h.Context(1 << log2w, G, cfg(1, ws_chunk_bytes=64, max_round_tx=1000)) as ctx:
+            ctx.load(start)
+            bases = np.cumsum([0] + sizes[:-1])
+            batches = [(t, submit(ctx, torch, wl.WORKLOAD_RMW, t, txid_base=int(bb)), int(bb))
+                       for t, bb in zip(txs, bases)]
+            if per_batch:
+                ctx.gpu_exec(per_batch=True)
+            _exec_and_check_replay(ctx, h, torch, start, batches, G, 64)
+
+
 @pytest.mark.parametrize("n_log", [0, 1, 31, 128, (1 << 16) + 77])
 def test_validation_planted(hetm, torch, n_log):
     """Validation-at-scale recipe at 2^20 words, ragged log sizes: flags, count, final."""
