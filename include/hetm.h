@@ -167,6 +167,12 @@ typedef struct hetm_config {
      * and hetm_cpu_log_write refuses writes), so that round validates clean.
      * 0 = off (default). */
     uint32_t starve_limit;
+    /* Wall-clock bound of the waits of one execution phase, in microseconds
+     * (0 = 20 s).  Past it every transaction not yet run gives up (status 2),
+     * the round reports HETM_ETIMEOUT and HETM_OUTCOME_GPU_ROLLED_BACK, and
+     * its merge undoes the whole batch (S -> W), as after a lost conflict.
+     * The error stays reported until hetm_load. */
+    uint32_t exec_budget_us;
 } hetm_config;
 
 #define HETM_POLICY_GPU_LOSES 0

@@ -48,7 +48,8 @@ class hetm_config(ctypes.Structure):
                 ("cache_key_base", _u64), ("cache_val_base", _u64), ("cache_lru_base", _u64),
                 ("cache_ver_base", _u64), ("exec_mode", _u32), ("early_validate", _u32),
                 ("max_round_tx", _u64), ("dev_alloc", _ALLOC), ("dev_free", _FREE),
-                ("alloc_user", _vp), ("conflict_policy", _u32), ("starve_limit", _u32)]
+                ("alloc_user", _vp), ("conflict_policy", _u32), ("starve_limit", _u32),
+                ("exec_budget_us", _u32)]
 
 
 class hetm_batch(ctypes.Structure):

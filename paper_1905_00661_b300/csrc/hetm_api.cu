@@ -336,7 +336,7 @@ ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
     a.prefix = prefix;
     a.next = &c->scr->next;
     a.max_attempts = c->cfg.max_attempts;
-    a.budget_ns = 20ull * 1000 * 1000 * 1000;
+    a.budget_ns = c->cfg.exec_budget_us ? 1000ull * c->cfg.exec_budget_us : 20ull * 1000 * 1000 * 1000;
     a.counters = c->scr->counters;
     a.err = &c->scr->err;
     if (c->early) {
@@ -432,7 +432,7 @@ int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e) {
     // CPU-loses: the GPU's writes stand whatever validation found (W -> S)
     if (c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES) force = 0;
     CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, force,
-                    &c->scr->dirty, c->stream_blocks, c->stream));
+                    &c->scr->dirty, c->stream_blocks, c->stream, &c->scr->err));
     CK(cudaMemcpyAsync(c->ws_host, c->ws, c->ws_words * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
     CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
@@ -970,7 +970,7 @@ int hetm_merge(hetm_ctx *c, int conflict) {
     CK(after_host_copies(c));
     CK(cudaMemsetAsync(&c->scr->dirty, 0, sizeof(unsigned long long), c->stream));
     CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, conflict,
-                    &c->scr->dirty, c->stream_blocks, c->stream));
+                    &c->scr->dirty, c->stream_blocks, c->stream, &c->scr->err));
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
     CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
@@ -1137,6 +1137,8 @@ int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     const bool cpu_loses = c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES;
     stats->outcome = !stats->conflict ? HETM_OUTCOME_CLEAN
                                       : (cpu_loses ? HETM_OUTCOME_CPU_DISCARDED : HETM_OUTCOME_GPU_ROLLED_BACK);
+    // a timed-out execution phase was undone by the merge whatever validation found
+    if (stats->err == HETM_ETIMEOUT) stats->outcome = HETM_OUTCOME_GPU_ROLLED_BACK;
     c->last_gpu_survived = stats->outcome != HETM_OUTCOME_GPU_ROLLED_BACK;
     // anti-starvation (Sec. IV-E): a read-only CPU phase ends with its round;
     // starve_limit consecutive GPU losses start one

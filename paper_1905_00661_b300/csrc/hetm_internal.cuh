@@ -232,9 +232,12 @@ cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int
                          const unsigned long long *skip_if = nullptr);
 cudaError_t launch_ts_max_if_clean(const DevRound *rp, uint32_t *ts, uint64_t n_words,
                                    const unsigned long long *conflicts, int blocks, cudaStream_t s);
+// err (may be null): a kErrTimeout there undoes the batch (S -> W) whatever
+// conflicts / force say
 cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_t *S,
                          uint64_t n_words, const unsigned long long *conflicts, int force,
-                         unsigned long long *dirty_count, int blocks, cudaStream_t s);
+                         unsigned long long *dirty_count, int blocks, cudaStream_t s,
+                         const int *err);
 // the serving loop's transactions-per-round capacity
 uint64_t server_max_round_tx(const hetm_server *s);
 cudaError_t launch_mark(const uint32_t *addr, const int32_t *vals, uint64_t n, int32_t *W,

@@ -147,17 +147,19 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
     // lane 0's clock decides for the whole warp, so the warp leaves together
     const unsigned long long t0 = __shfl_sync(kFull, globaltimer_ns(), 0);
     uint32_t iter = 0;
+    bool expired = false;  // past the budget: draw what is left only to report it
 
     for (;;) {
         // wall-clock bound: past it, every unfinished transaction gives up
-        if ((++iter & 63u) == 0 &&
+        if (!expired && (++iter & 63u) == 0 &&
             __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns) {
+            expired = true;
             if (gi != kNone) {
                 if (o_status) o_status[li] = kGaveUp;
                 ++n_gaveup;
+                gi = kNone;
             }
             if (lane == 0) set_err(a.err, kErrTimeout);
-            break;
         }
         // ---------------------------------------------------- draw new work
         const bool need = gi == kNone && !done;
@@ -215,6 +217,10 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
                         gi = kNone;  // drawn again next iteration
                     } else if (a.skip_ro && wl == HETM_WL_RMW && !upd) {
                         gi = kNone;  // ran in the read-only phase
+                    } else if (expired) {
+                        if (o_status) o_status[li] = kGaveUp;
+                        ++n_gaveup;
+                        gi = kNone;
                     }
                 } else {
                     done = true;

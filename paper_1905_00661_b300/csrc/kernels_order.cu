@@ -687,23 +687,30 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
     for (;;) {
         if (t == 0) {
             // sm.abort: 1 = the time budget ran out, 2 = early validation
-            // found a conflict; either way this CTA takes no new segment
+            // found a conflict; either way this CTA runs no more transactions
+            // and only reports the ones of the segments it still takes
             if (!sm.abort && a.stop && ld_rlx32((const int32_t *)a.stop)) sm.abort = 2;
-            sm.seg = sm.abort == 1 ? 0xFFFFFFFFu : (uint32_t)atomicAdd(a.next, 1ull);
+            sm.seg = (uint32_t)atomicAdd(a.next, 1ull);
             sm.n_list = 0;
         }
         __syncthreads();
         const uint32_t g = sm.seg;
         if (g >= n_seg) break;
         const unsigned long long tag = (unsigned long long)(g + 1) << 32;
-        if (sm.abort == 2) {
-            // stopped by early validation: the rest of the phase only reports
-            // its transactions as not run
+        if (sm.abort) {
+            // stopped by early validation (the round is lost to the CPU: not
+            // run) or past the time budget (gave up; cache requests are left
+            // to k_cache_runs, and the merge undoes the whole phase)
             const uint32_t r = g * SEG + t;
             if (!poller && r < n_ord) {
                 const OrdRec &q = o.rec[r];
                 const DevBatch &d = a.batches[q.meta >> 16];
-                if (d.status) d.status[q.li] = kNotRun;
+                if (sm.abort == 2) {
+                    if (d.status) d.status[q.li] = kNotRun;
+                } else if (((q.meta >> 3) & 3u) != HETM_WL_CACHE) {
+                    if (d.status) d.status[q.li] = kGaveUp;
+                    ++n_gaveup;
+                }
             }
             __syncthreads();
             if (t == 0 && a.segs_done) atomicAdd(a.segs_done, 1u);
@@ -973,10 +980,10 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 if (o_status) o_status[rc.li] = kGaveUp;
                 ++n_gaveup;
                 set_err(a.err, kErrTimeout);
+                // the other warps of the CTA see it at their next idle pass and
+                // give up too; a successor waiting on this transaction never
+                // sees its input arrive, so it cannot run on a missing value
                 sm.abort = 1;
-                // release local successors so that they end too
-#pragma unroll
-                for (int k = 0; k < 4; ++k) *(volatile unsigned long long *)&sm.pack[k][t] = tag;
             }
         }
         __syncthreads();  // end of segment

@@ -348,8 +348,11 @@ __device__ __forceinline__ bool chunk_dirty(const uint32_t *ws, uint64_t c) {
 __global__ void __launch_bounds__(256) k_merge(const uint32_t *__restrict__ ws, uint32_t cshift,
                                                int32_t *W, int32_t *S, uint64_t n_words,
                                                const unsigned long long *conflicts, int force,
-                                               unsigned long long *dirty_count) {
-    const bool conflict = force >= 0 ? force != 0 : (*conflicts != 0ull);
+                                               unsigned long long *dirty_count, const int *err) {
+    // an execution phase that ran out of its time budget is undone like a
+    // batch that lost a conflict (its transactions ran only in part)
+    const bool conflict =
+        (err && *err == kErrTimeout) || (force >= 0 ? force != 0 : (*conflicts != 0ull));
     const uint4 *src = reinterpret_cast<const uint4 *>(conflict ? S : W);
     uint4 *dst = reinterpret_cast<uint4 *>(conflict ? W : S);
     const unsigned lane = threadIdx.x & 31u;
@@ -488,8 +491,9 @@ cudaError_t launch_ts_max_if_clean(const DevRound *rp, uint32_t *ts, uint64_t n_
 
 cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_t *S,
                          uint64_t n_words, const unsigned long long *conflicts, int force,
-                         unsigned long long *dirty_count, int blocks, cudaStream_t s) {
-    k_merge<<<blocks, 256, 0, s>>>(ws, cshift, W, S, n_words, conflicts, force, dirty_count);
+                         unsigned long long *dirty_count, int blocks, cudaStream_t s,
+                        const int *err) {
+    k_merge<<<blocks, 256, 0, s>>>(ws, cshift, W, S, n_words, conflicts, force, dirty_count, err);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ def test_record_layouts_match_workloads():
     import workloads as wl
     assert h.LOG_DTYPE == wl.LOG_DTYPE
     assert ctypes.sizeof(h.hetm_batch) == 48
-    assert ctypes.sizeof(h.hetm_config) == 136
+    assert ctypes.sizeof(h.hetm_config) == 144
     assert ctypes.sizeof(h.hetm_round_stats) == 96
 
 
