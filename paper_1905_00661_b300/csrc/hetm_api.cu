@@ -729,6 +729,7 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
 }
 
 int hetm_load(hetm_ctx *c, const int32_t *src, uint64_t n) {
+    const Range range("hetm_load");
     if (!c || !src || n != c->n_words) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->ship));
@@ -857,6 +858,7 @@ static int end_round(hetm_ctx *c, uint64_t r, int force) {
 }
 
 int hetm_gpu_exec(hetm_ctx *c, int per_batch) {
+    const Range range("hetm_gpu_exec");
     if (!c) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     if (c->pending.empty()) return HETM_OK;
@@ -921,6 +923,7 @@ int hetm_log_attach(hetm_ctx *c, const hetm_log_entry *dev_log, uint64_t n) {
 }
 
 int hetm_validate(hetm_ctx *c, uint64_t *n_conflicts, uint32_t *dev_flag_bits) {
+    const Range range("hetm_validate");
     if (!c) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     const hetm_log_entry *log = nullptr;
@@ -965,6 +968,7 @@ int hetm_validate_only(hetm_ctx *c, const hetm_log_entry *dev_log, uint64_t n,
 }
 
 int hetm_merge(hetm_ctx *c, int conflict) {
+    const Range range("hetm_merge");
     if (!c || conflict < -1 || conflict > 1) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(after_host_copies(c));
@@ -983,6 +987,7 @@ int hetm_merge(hetm_ctx *c, int conflict) {
 }
 
 int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
+    const Range range("hetm_round");
     if (!c) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     if (!c->g_exec) {
@@ -1040,6 +1045,7 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
 }
 
 int hetm_read_dirty(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_bytes) {
+    const Range range("hetm_read_dirty");
     if (!c || !host) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
@@ -1069,6 +1075,7 @@ int hetm_read_dirty(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_
 }
 
 int hetm_read_dirty_async(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_bytes) {
+    const Range range("hetm_read_dirty_async");
     if (!c || !host) return HETM_EINVAL;
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));  // the dirty map and outcome of the last round
@@ -1110,6 +1117,7 @@ int hetm_read_dirty_wait(hetm_ctx *c) {
 int hetm_cpu_updates_allowed(hetm_ctx *c) { return c && !c->cpu_read_only.load() ? 1 : 0; }
 
 int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
+    const Range range("hetm_round_wait");
     if (!c) return HETM_EINVAL;
     CK(cudaEventSynchronize(c->ev[5]));
     if (!c->round_open) {

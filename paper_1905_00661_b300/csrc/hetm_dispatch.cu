@@ -279,6 +279,7 @@ void controller(hetm_dispatch *d) {
         }
         const hetm_tx_type tt = a->ty->t;
         lk.unlock();
+        const hetm::Range range("hetm_dispatch activation");
         // pack the records of the batch
         const size_t rb = tt.rec_bytes, ob = tt.out_bytes;
         a->tx.resize((size_t)a->n * rb);

@@ -2,11 +2,21 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "hetm.h"
 
 namespace hetm {
+
+// Host-side NVTX range over one library call (what the host enqueued, and
+// when): visible to a profiler that is attached, free otherwise.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 constexpr uint8_t kCommitted = 1;
 constexpr uint8_t kGaveUp = 2;

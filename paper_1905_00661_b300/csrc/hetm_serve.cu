@@ -161,6 +161,7 @@ void finish(hetm_server *s, std::vector<Req *> &group, int rc) {
 // Launch one round for `group` (already staged): the executor waits for
 // the staging copies; result copies are queued behind the round.
 int launch_round(hetm_server *s, std::vector<Req *> &group) {
+    const hetm::Range range("hetm_server round");
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return HETM_ECUDA;
     cudaEventRecord(ev, s->copy);
