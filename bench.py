@@ -36,8 +36,8 @@ import workloads as wl  # noqa: E402
 
 # DRAM bytes (read + write) of the ordered-phase kernel per transaction of the
 # round, from one ncu capture of `bench.py --case rmw_small` (1M transactions,
-# 35.42 MB + 0.52 MB), scaled to a launch by the transaction count.
-TRAFFIC_SEG_EXEC_PER_TX = (35.417e6 + 0.519e6) / (1 << 20)
+# 35.53 MB + 0.61 MB), scaled to a launch by the transaction count.
+TRAFFIC_SEG_EXEC_PER_TX = (35.527e6 + 0.610e6) / (1 << 20)
 # autotuner search space of the main step (both executors, three CTA sizes,
 # the granules of Sec. V-A's study and three merge chunks)
 TUNE_SPACE = {"modes": 3, "threads": [128, 256, 512], "blocks_per_sm": [0],
