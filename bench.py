@@ -201,9 +201,10 @@ def bench_ours(args, rank, world, local_rank, inputs):
 
     # ---- e2e: host-resident inputs and results, copies inside the timed region.
     # Pipelined through the public asynchronous round (hetm_round without
-    # stats, hetm_round_wait): while round i runs, round i+1's transactions
-    # go H2D on a copy stream and its CPU log is written by the host threads,
-    # and round i-1's results come back D2H.
+    # stats, hetm_round_wait; two rounds in flight): while round i runs, round
+    # i+1's transactions go H2D on a copy stream, its CPU log is written by the
+    # host threads and it is launched behind round i, and round i-1's results
+    # come back D2H.
     e2e_rounds = max(3, K)
     r0 = W + K
     # host-side CPU logs of every e2e round, prepared before timing (workload generation)
@@ -220,6 +221,7 @@ def bench_ours(args, rank, world, local_rank, inputs):
     cs = torch.cuda.Stream()
     ev_h2d = [torch.cuda.Event() for _ in range(2)]
     ev_d2h = [torch.cuda.Event() for _ in range(2)]
+    ev_end = [torch.cuda.Event() for _ in range(2)]  # end of the round using slot i
     for e in ev_d2h:
         e.record(cs)
 
@@ -241,6 +243,7 @@ def bench_ours(args, rank, world, local_rank, inputs):
         ctx.submit_batch(h.HETM_WL_RMW, dbuf[slot], o_, st_, out_, txid_base=(r * N_TX) & 0xFFFFFFFF,
                          n_tx=N_TX)
         ctx.round(stats=False)
+        ev_end[slot].record(s)
 
     def e2e_pass(first, n_rounds):
         committed = 0
@@ -252,19 +255,16 @@ def bench_ours(args, rank, world, local_rank, inputs):
             if r + 1 < first + n_rounds:
                 stage_tx(r + 1, slot ^ 1)
                 write_logs(r + 1)
-            st = ctx.round_wait()
+                launch(r + 1, slot ^ 1)   # queued on the device behind round r
+            st = ctx.round_wait()          # round r
             if st["rc"] != h.HETM_OK:
                 raise RuntimeError(f"round failed: {st}")
             committed += 0 if st["conflict"] else st["committed"]
-            done = torch.cuda.Event()
-            done.record(s)
-            cs.wait_event(done)
+            cs.wait_event(ev_end[slot])
             with torch.cuda.stream(cs):
                 for dst, src in zip(hout[slot], dout[slot]):
                     dst.copy_(src, non_blocking=True)
                 ev_d2h[slot].record(cs)
-            if r + 1 < first + n_rounds:
-                launch(r + 1, slot ^ 1)
         cs.synchronize()
         return committed
 

@@ -350,13 +350,21 @@ typedef struct hetm_round_stats {
 #define HETM_OUTCOME_CPU_DISCARDED 2  /* conflict, CPU loses: its log is discarded */
 
 /* One whole round: run the queued batches (persistent executor), ship the
- * CPU logs, validate, apply, merge, clear.  The device part is a CUDA graph
+ * CPU logs, validate, apply, merge, clear.  The device part is CUDA graphs
  * captured on first use and replayed.  stats NULL = asynchronous (no host
- * synchronization); otherwise waits and fills *stats. */
+ * synchronization): up to two rounds may be in flight, the second queued on
+ * the device behind the first (its batches and CPU log are the ones
+ * submitted before this call), so that the GPU does not wait for the host
+ * to collect a round before the next starts; HETM_EBUSY with two in flight.
+ * Otherwise (stats non-NULL) it needs none in flight (HETM_EBUSY), waits
+ * and fills *stats.  With two rounds in flight, the anti-starvation rule set
+ * by the first applies to the execution phase launched after it is
+ * collected. */
 HETM_API int hetm_round(hetm_ctx *ctx, hetm_round_stats *stats);
 
-/* Wait for the round last launched by hetm_round(ctx, NULL) and fill *stats
- * (may be NULL).  Returns the round's status like hetm_round. */
+/* Wait for the oldest round launched by hetm_round(ctx, NULL) and not yet
+ * collected, and fill *stats (may be NULL; zeroed when none is in flight).
+ * Returns the round's status like hetm_round. */
 HETM_API int hetm_round_wait(hetm_ctx *ctx, hetm_round_stats *stats);
 
 /* Where a submitted batch is, without blocking (the GPU-controller's view of
@@ -396,7 +404,9 @@ HETM_API int hetm_batch_poll(hetm_ctx *ctx, uint64_t batch_id, hetm_batch_result
  * in one copy.  After a round the GPU lost nothing is copied (the host
  * replica already holds the round's outcome).  Under CPU_LOSES the caller
  * first restores the words its discarded log wrote from its own shadow.
- * *n_chunks / *n_bytes (may be NULL) get what was copied.  Synchronous. */
+ * *n_chunks / *n_bytes (may be NULL) get what was copied.  Synchronous.
+ * HETM_EBUSY while a round is in flight (it would change STMR^S under the
+ * copies): collect it with hetm_round_wait first. */
 HETM_API int hetm_read_dirty(hetm_ctx *ctx, int32_t *host_stmr, uint64_t *n_chunks, uint64_t *n_bytes);
 
 /* Double-buffered form of hetm_read_dirty (Sec. IV-D: the shadow STMR^S lets

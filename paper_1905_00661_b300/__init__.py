@@ -552,12 +552,14 @@ class Context:
             if rc not in (HETM_OK, HETM_EDEVICE, HETM_ETIMEOUT):
                 raise HetmError(rc, "hetm_round")
             return d
-        _ck(_lib.hetm_round(self.h, None), "hetm_round")
+        rc = _lib.hetm_round(self.h, None)
         self._leave()
+        _ck(rc, "hetm_round")
         return None
 
     def round_wait(self):
-        """Wait for the round last started by ``round(stats=False)``; its stats."""
+        """Wait for the oldest round started by ``round(stats=False)`` and not yet
+        collected (two may be in flight); its stats."""
         st = hetm_round_stats()
         rc = _lib.hetm_round_wait(self.h, ctypes.byref(st))
         d = st.as_dict()

@@ -95,15 +95,18 @@ struct hetm_ctx {
     uint64_t *d_prefix0 = nullptr; // {0} for single-batch launches
     hetm_log_entry *dlog[2] = {nullptr, nullptr};
 
-    // pinned staging of the batch table (two slots, alternating)
+    // pinned staging of the batch table: two stagings per round (batches at
+    // its start, the CPU log after the execution phase is launched), for two
+    // rounds in flight; a slot is refilled once its copies are done
+    static constexpr int kStages = 4;
     struct Stage {
         DevRound *rounds = nullptr;
         DevBatch *batches = nullptr;
         uint64_t *prefix = nullptr;
         cudaEvent_t used = nullptr;
-    } stage[2];
+    } stage[kStages];
     int stage_cur = 0;
-    RoundOut *out = nullptr;       // pinned
+    RoundOut *out = nullptr;       // pinned: [0] hetm_validate, [1 + slot] a round in flight
 
     std::vector<DevBatch> pending;
     std::vector<uint64_t> pending_ids;  // ids of `pending`, same order
@@ -140,13 +143,22 @@ struct hetm_ctx {
     std::atomic<int> ship_err{0};
 
     // graphs
-    cudaGraphExec_t g_exec = nullptr, g_sync = nullptr;
+    // Up to kInFlight rounds launched by hetm_round(ctx, NULL) and not yet
+    // collected by hetm_round_wait, oldest at slot r_head.  Each slot has its
+    // own sync graph, timing events, pinned results and WS_bmp copy, so a
+    // round can be launched before the previous one is collected.
+    static constexpr int kInFlight = 2;
+    cudaGraphExec_t g_exec = nullptr, g_sync[kInFlight] = {};
     uint32_t n_kern[2] = {0, 0};  // kernel nodes of g_exec / g_sync
-    cudaEvent_t ev[7] = {};  // round timing: 0/6 around the executor, 1..4 in the sync graph, 5 end
+    cudaEvent_t ev[kInFlight][7] = {};  // timing: 0/6 around the executor, 1..4 in the sync graph, 5 end
+    uint64_t slot_n_log[kInFlight] = {};
+    uint32_t slot_nb[kInFlight] = {};
+    int r_head = 0, r_open = 0;
     // conflict policy: WS_bmp of the last round (pinned host copy, for
     // hetm_read_dirty), whether that round's GPU writes survived, and the
     // anti-starvation state
-    uint32_t *ws_host = nullptr;
+    uint32_t *ws_host = nullptr;   // kInFlight copies, one per round slot
+    const uint32_t *ws_last = nullptr;  // the copy of the last collected round
     bool last_gpu_survived = false;
     uint32_t gpu_losses = 0;
     std::atomic<bool> cpu_read_only{false};
@@ -171,10 +183,6 @@ struct hetm_ctx {
     unsigned long long prev_counters[3] = {0, 0, 0};
 
     std::vector<void *> dev_allocs;
-    // the last round launched by hetm_round (read back by hetm_round_wait)
-    uint64_t last_n_log = 0;
-    uint32_t last_nb = 0;
-    bool round_open = false;
 };
 
 #define CK(x)                                                                       \
@@ -313,7 +321,7 @@ int stage_round(hetm_ctx *c, const hetm_log_entry *log, uint64_t n_log) {
                            cudaMemcpyHostToDevice, c->stream));
     }
     CK(cudaEventRecord(st.used, c->stream));
-    c->stage_cur ^= 1;
+    c->stage_cur = (c->stage_cur + 1) % hetm_ctx::kStages;
     return HETM_OK;
 }
 
@@ -423,7 +431,8 @@ int enqueue_validate_apply(hetm_ctx *c, uint32_t *flags, cudaEvent_t *e) {
 
 // validate (+ TS max) -> apply -> merge -> clear; events e[0..3] between
 // phases when non-null.
-int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e) {
+int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e, RoundOut *out,
+                 uint32_t *ws_dst) {
     CK(cudaMemsetAsync(&c->scr->conflicts, 0, 2 * sizeof(unsigned long long), c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[0], c->stream, cudaEventRecordExternal));
     int rc = enqueue_validate_apply(c, flags, e);
@@ -433,23 +442,26 @@ int enqueue_sync(hetm_ctx *c, uint32_t *flags, int force, cudaEvent_t *e) {
     if (c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES) force = 0;
     CK(launch_merge(c->ws, c->cshift, c->W, c->S, c->n_words, &c->scr->conflicts, force,
                     &c->scr->dirty, c->stream_blocks, c->stream, &c->scr->err));
-    CK(cudaMemcpyAsync(c->ws_host, c->ws, c->ws_words * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(ws_dst, c->ws, c->ws_words * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemsetAsync(c->rs, 0, c->rs_words * 4, c->stream));
     CK(cudaMemsetAsync(c->filter, 0, kFilterBits / 8, c->stream));
     CK(cudaMemsetAsync(c->ws, 0, c->ws_words * 4, c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[3], c->stream, cudaEventRecordExternal));
-    CK(cudaMemcpyAsync(c->out, c->scr->counters, 5 * sizeof(unsigned long long),
+    CK(cudaMemcpyAsync(out, c->scr->counters, 5 * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&c->out->err, &c->scr->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&c->out->stopped, &c->scr->stop, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(&out->err, &c->scr->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&out->stopped, &c->scr->stop, sizeof(unsigned int), cudaMemcpyDeviceToHost,
                        c->stream));
     return HETM_OK;
 }
 
-int capture(hetm_ctx *c, cudaGraphExec_t *out, int which) {
+// which: 0 = the execution phase, 1 = the sync phase of round slot `slot`
+int capture(hetm_ctx *c, cudaGraphExec_t *out, int which, int slot = 0) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = which == 0 ? enqueue_exec(c, false, 0, true) : enqueue_sync(c, nullptr, -1, c->ev + 1);
+    int rc = which == 0 ? enqueue_exec(c, false, 0, true)
+                        : enqueue_sync(c, nullptr, -1, c->ev[slot] + 1, c->out + 1 + slot,
+                                       c->ws_host + (size_t)slot * c->ws_words);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc != HETM_OK) {
         if (g) cudaGraphDestroy(g);
@@ -521,8 +533,10 @@ void hetm_destroy(hetm_ctx *c) {
     if (c->ship) cudaStreamSynchronize(c->ship);
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->g_exec) cudaGraphExecDestroy(c->g_exec);
-    if (c->g_sync) cudaGraphExecDestroy(c->g_sync);
-    for (auto &e : c->ev)
+    for (auto &g : c->g_sync)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto &slot : c->ev)
+        for (auto &e : slot)
         if (e) cudaEventDestroy(e);
     for (auto &s : c->stage) {
         if (s.rounds) cudaFreeHost(s.rounds);
@@ -669,9 +683,12 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         if (cudaEventCreateWithFlags(&s.used, cudaEventDisableTiming) != cudaSuccess)
             return fail(HETM_ECUDA);
     }
-    if (!host_alloc_t(&c->out, 1) || !host_alloc_t(&c->ws_host, c->ws_words)) return fail(HETM_ENOMEM);
-    std::memset(c->ws_host, 0, c->ws_words * 4);
-    std::memset(c->out, 0, sizeof(RoundOut));
+    if (!host_alloc_t(&c->out, 1 + hetm_ctx::kInFlight) ||
+        !host_alloc_t(&c->ws_host, hetm_ctx::kInFlight * c->ws_words))
+        return fail(HETM_ENOMEM);
+    std::memset(c->ws_host, 0, hetm_ctx::kInFlight * c->ws_words * 4);
+    std::memset(c->out, 0, (1 + hetm_ctx::kInFlight) * sizeof(RoundOut));
+    c->ws_last = c->ws_host;
     for (int i = 0; i < 2; ++i) {
         if (cudaEventCreateWithFlags(&c->dlog_free[i], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->tlog_free[i], cudaEventDisableTiming) != cudaSuccess)
@@ -679,8 +696,9 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
     }
     if (cudaEventCreateWithFlags(&c->ship_done, cudaEventDisableTiming) != cudaSuccess)
         return fail(HETM_ECUDA);
-    for (auto &e : c->ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return fail(HETM_ECUDA);
+    for (auto &slot : c->ev)
+        for (auto &e : slot)
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(HETM_ECUDA);
     for (auto &e : c->rend)
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(HETM_ECUDA);
     if (cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking) != cudaSuccess ||
@@ -719,10 +737,11 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         return fail(HETM_ECUDA);
     for (int i = 0; i < 2; ++i) {
         if (cudaEventRecord(c->dlog_free[i], c->stream) != cudaSuccess ||
-            cudaEventRecord(c->tlog_free[i], c->ship) != cudaSuccess ||
-            cudaEventRecord(c->stage[i].used, c->stream) != cudaSuccess)
+            cudaEventRecord(c->tlog_free[i], c->ship) != cudaSuccess)
             return fail(HETM_ECUDA);
     }
+    for (auto &st : c->stage)
+        if (cudaEventRecord(st.used, c->stream) != cudaSuccess) return fail(HETM_ECUDA);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(HETM_ECUDA);
     *out = c;
     return HETM_OK;
@@ -761,6 +780,9 @@ int hetm_load(hetm_ctx *c, const int32_t *src, uint64_t n) {
     c->attached = nullptr;
     c->attached_n = 0;
     std::memset(c->prev_counters, 0, sizeof(c->prev_counters));
+    // rounds still in flight have finished (stream synchronized) and are discarded
+    c->r_open = 0;
+    c->r_head = 0;
     return HETM_OK;
 }
 
@@ -989,22 +1011,26 @@ int hetm_merge(hetm_ctx *c, int conflict) {
 int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
     const Range range("hetm_round");
     if (!c) return HETM_EINVAL;
+    // the synchronous form collects its own round: no other may be in flight
+    if (c->r_open == hetm_ctx::kInFlight || (stats && c->r_open)) return HETM_EBUSY;
     CK(cudaSetDevice(c->device));
+    const int slot = (c->r_head + c->r_open) % hetm_ctx::kInFlight;
     if (!c->g_exec) {
         int rc = capture(c, &c->g_exec, 0);
         if (rc != HETM_OK) return rc;
     }
-    if (!c->g_sync) {
-        int rc = capture(c, &c->g_sync, 1);
+    if (!c->g_sync[slot]) {
+        int rc = capture(c, &c->g_sync[slot], 1, slot);
         if (rc != HETM_OK) return rc;
     }
+    cudaEvent_t *ev = c->ev[slot];
     const uint32_t nb = (uint32_t)c->pending.size();
     // the executor starts right away; log chunks keep shipping meanwhile
     int rc = stage_round(c, nullptr, 0);
     if (rc != HETM_OK) return rc;
-    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(cudaEventRecord(ev[0], c->stream));
     if (nb) CK(cudaGraphLaunch(c->g_exec, c->stream));
-    CK(cudaEventRecord(c->ev[6], c->stream));
+    CK(cudaEventRecord(ev[6], c->stream));
     c->pending.clear();
     if (nb || c->exec_round) {
         if (!c->exec_round) c->exec_round = ++c->round_seq;
@@ -1029,17 +1055,17 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
     }
     CK(cudaStreamWaitEvent(c->stream, c->ship_done, 0));
     CK(after_host_copies(c));  // the execution phase above overlapped them
-    CK(cudaGraphLaunch(c->g_sync, c->stream));
+    CK(cudaGraphLaunch(c->g_sync[slot], c->stream));
     CK(cudaEventRecord(c->dlog_free[c->dlog_cur ^ 1], c->stream));
     if (c->exec_round) {
         rc = end_round(c, c->exec_round, c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES ? 0 : -1);
         c->exec_round = 0;
         if (rc != HETM_OK) return rc;
     }
-    CK(cudaEventRecord(c->ev[5], c->stream));
-    c->last_n_log = n;
-    c->last_nb = nb;
-    c->round_open = true;
+    CK(cudaEventRecord(ev[5], c->stream));
+    c->slot_n_log[slot] = n;
+    c->slot_nb[slot] = nb;
+    ++c->r_open;
     if (!stats) return HETM_OK;
     return hetm_round_wait(c, stats);
 }
@@ -1047,6 +1073,7 @@ int hetm_round(hetm_ctx *c, hetm_round_stats *stats) {
 int hetm_read_dirty(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_bytes) {
     const Range range("hetm_read_dirty");
     if (!c || !host) return HETM_EINVAL;
+    if (c->r_open) return HETM_EBUSY;  // a round in flight would change S under the copies
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
     uint64_t chunks = 0, bytes = 0;
@@ -1055,12 +1082,12 @@ int hetm_read_dirty(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_
         const uint64_t n_chunk = (c->n_words + wpc - 1) / wpc;
         uint64_t ch = 0;
         while (ch < n_chunk) {
-            if (!((c->ws_host[ch >> 5] >> (ch & 31)) & 1u)) {
+            if (!((c->ws_last[ch >> 5] >> (ch & 31)) & 1u)) {
                 ++ch;
                 continue;
             }
             uint64_t end = ch + 1;  // coalesce a run of dirty chunks into one copy
-            while (end < n_chunk && ((c->ws_host[end >> 5] >> (end & 31)) & 1u)) ++end;
+            while (end < n_chunk && ((c->ws_last[end >> 5] >> (end & 31)) & 1u)) ++end;
             const uint64_t w0 = ch * wpc, w1 = std::min<uint64_t>(end * wpc, c->n_words);
             CK(cudaMemcpyAsync(host + w0, c->S + w0, (w1 - w0) * 4, cudaMemcpyDeviceToHost, c->stream));
             chunks += end - ch;
@@ -1077,6 +1104,7 @@ int hetm_read_dirty(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_
 int hetm_read_dirty_async(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64_t *n_bytes) {
     const Range range("hetm_read_dirty_async");
     if (!c || !host) return HETM_EINVAL;
+    if (c->r_open) return HETM_EBUSY;  // a round in flight would change S under the copies
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));  // the dirty map and outcome of the last round
     uint64_t chunks = 0, bytes = 0;
@@ -1087,12 +1115,12 @@ int hetm_read_dirty_async(hetm_ctx *c, int32_t *host, uint64_t *n_chunks, uint64
         const uint64_t n_chunk = (c->n_words + wpc - 1) / wpc;
         uint64_t ch = 0;
         while (ch < n_chunk) {
-            if (!((c->ws_host[ch >> 5] >> (ch & 31)) & 1u)) {
+            if (!((c->ws_last[ch >> 5] >> (ch & 31)) & 1u)) {
                 ++ch;
                 continue;
             }
             uint64_t end = ch + 1;
-            while (end < n_chunk && ((c->ws_host[end >> 5] >> (end & 31)) & 1u)) ++end;
+            while (end < n_chunk && ((c->ws_last[end >> 5] >> (end & 31)) & 1u)) ++end;
             const uint64_t w0 = ch * wpc, w1 = std::min<uint64_t>(end * wpc, c->n_words);
             CK(cudaMemcpyAsync(host + w0, c->S + w0, (w1 - w0) * 4, cudaMemcpyDeviceToHost, c->d2h));
             chunks += end - ch;
@@ -1119,29 +1147,35 @@ int hetm_cpu_updates_allowed(hetm_ctx *c) { return c && !c->cpu_read_only.load()
 int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     const Range range("hetm_round_wait");
     if (!c) return HETM_EINVAL;
-    CK(cudaEventSynchronize(c->ev[5]));
-    if (!c->round_open) {
+    if (!c->r_open) {
         if (stats) std::memset(stats, 0, sizeof(*stats));
         return HETM_OK;
     }
-    c->round_open = false;
-    const uint64_t n = c->last_n_log;
-    const uint32_t nb = c->last_nb;
+    // the oldest round in flight
+    const int slot = c->r_head;
+    cudaEvent_t *ev = c->ev[slot];
+    CK(cudaEventSynchronize(ev[5]));
+    c->r_head = (c->r_head + 1) % hetm_ctx::kInFlight;
+    --c->r_open;
+    c->ws_last = c->ws_host + (size_t)slot * c->ws_words;
+    const RoundOut *out = c->out + 1 + slot;
+    const uint64_t n = c->slot_n_log[slot];
+    const uint32_t nb = c->slot_nb[slot];
     hetm_round_stats local;
     if (!stats) stats = &local;
     std::memset(stats, 0, sizeof(*stats));
     stats->n_log = n;
-    stats->n_conflicts = c->out->conflicts;
-    stats->conflict = c->out->conflicts != 0;
-    stats->err = c->out->err == 0 ? HETM_OK : (c->out->err == kErrTimeout ? HETM_ETIMEOUT : HETM_EDEVICE);
-    stats->committed = c->out->counters[0] - c->prev_counters[0];
-    stats->gave_up = c->out->counters[1] - c->prev_counters[1];
-    stats->aborts = c->out->counters[2] - c->prev_counters[2];
-    std::memcpy(c->prev_counters, c->out->counters, sizeof(c->prev_counters));
-    stats->dirty_chunks = c->out->dirty;
+    stats->n_conflicts = out->conflicts;
+    stats->conflict = out->conflicts != 0;
+    stats->err = out->err == 0 ? HETM_OK : (out->err == kErrTimeout ? HETM_ETIMEOUT : HETM_EDEVICE);
+    stats->committed = out->counters[0] - c->prev_counters[0];
+    stats->gave_up = out->counters[1] - c->prev_counters[1];
+    stats->aborts = out->counters[2] - c->prev_counters[2];
+    std::memcpy(c->prev_counters, out->counters, sizeof(c->prev_counters));
+    stats->dirty_chunks = out->dirty;
     stats->n_batches = nb;
     stats->n_kernels = (nb ? c->n_kern[0] : 0) + c->n_kern[1] + (c->early && nb && n ? 1u : 0u);
-    stats->stopped_early = c->early && nb && n ? c->out->stopped : 0u;
+    stats->stopped_early = c->early && nb && n ? out->stopped : 0u;
     const bool cpu_loses = c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES;
     stats->outcome = !stats->conflict ? HETM_OUTCOME_CLEAN
                                       : (cpu_loses ? HETM_OUTCOME_CPU_DISCARDED : HETM_OUTCOME_GPU_ROLLED_BACK);
@@ -1160,11 +1194,11 @@ int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
         }
     }
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[6]) == cudaSuccess) stats->ms_exec = ms;
-    if (cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]) == cudaSuccess) stats->ms_validate = ms;
-    if (cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]) == cudaSuccess) stats->ms_apply = ms;
-    if (cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]) == cudaSuccess) stats->ms_merge = ms;
-    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]) == cudaSuccess) stats->ms_total = ms;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[6]) == cudaSuccess) stats->ms_exec = ms;
+    if (cudaEventElapsedTime(&ms, ev[1], ev[2]) == cudaSuccess) stats->ms_validate = ms;
+    if (cudaEventElapsedTime(&ms, ev[2], ev[3]) == cudaSuccess) stats->ms_apply = ms;
+    if (cudaEventElapsedTime(&ms, ev[3], ev[4]) == cudaSuccess) stats->ms_merge = ms;
+    if (cudaEventElapsedTime(&ms, ev[0], ev[5]) == cudaSuccess) stats->ms_total = ms;
     return stats->err;
 }
 
