@@ -511,18 +511,34 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
         if (d.status) d.status[li] = kCommitted;
         return true;
     };
-    // loop bound rounded up to whole warps so that the warp collectives below are convergent
-    const uint64_t span = (total + 31) & ~31ull;
-    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < span; u += stride) {
+    // the indices left to the STM are appended block by block (one atomic per
+    // block and iteration: a counter per warp would serialize 1 in 32 of all
+    // transactions on one word); the trip count is uniform over the block so
+    // that its barriers are
+    __shared__ uint32_t warp_off[2][8];
+    __shared__ unsigned long long blk_base[2];
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    uint32_t it = 0;
+    for (uint64_t ub = blockIdx.x * (uint64_t)blockDim.x; ub < total; ub += stride, it ^= 1u) {
+        const uint64_t u = ub + threadIdx.x;
         const bool ran = u < total && run_ro(u);
         n_commit += ran ? 1u : 0u;
-        if (listing) {  // the indices left to the STM, appended warp by warp
+        if (listing) {
             const bool left = u < total && !ran;
             const unsigned m = __ballot_sync(kFull, left);
-            unsigned long long base = 0;
-            if (m && (threadIdx.x & 31u) == 0) base = atomicAdd(a.rest_n, (unsigned long long)__popc(m));
-            base = __shfl_sync(kFull, base, 0);
-            if (left) a.rest[base + __popc(m & lanemask_lt())] = (uint32_t)u;
+            if (lane == 0) warp_off[it][wid] = __popc(m);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t sum = 0;
+                for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) {
+                    const uint32_t c = warp_off[it][w];
+                    warp_off[it][w] = sum;
+                    sum += c;
+                }
+                blk_base[it] = sum ? atomicAdd(a.rest_n, (unsigned long long)sum) : 0ull;
+            }
+            __syncthreads();
+            if (left) a.rest[blk_base[it] + warp_off[it][wid] + __popc(m & lanemask_lt())] = (uint32_t)u;
         }
     }
 #pragma unroll
