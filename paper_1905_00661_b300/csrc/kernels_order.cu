@@ -427,12 +427,24 @@ __global__ void __launch_bounds__(256) k_ord_emit(OrderArgs o) {
 __global__ void __launch_bounds__(256) k_ord_runs(OrderArgs o) {
     const uint32_t n = *o.n_acc;
     const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const bool head = i == 0 || o.keys0[i] != o.keys0[i - 1];
-        const bool writer = o.vals0[i] & 1u;
-        o.runs[i] = ((head ? i : 0ull) << 32) | (writer ? i + 1 : 0ull);
-        o.packed[i] = 0ull;
-        if (head && (o.vals0[i] & 2u)) o.cache_heads[atomicAdd(o.n_cache_runs, 1u)] = (uint32_t)i;
+    // bound rounded up to whole warps: the cache run heads are appended warp by warp
+    const uint64_t span = (n + 31ull) & ~31ull;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < span; i += stride) {
+        bool cache_head = false;
+        if (i < n) {
+            const bool head = i == 0 || o.keys0[i] != o.keys0[i - 1];
+            const uint32_t v = o.vals0[i];
+            o.runs[i] = ((head ? i : 0ull) << 32) | ((v & 1u) ? i + 1 : 0ull);
+            o.packed[i] = 0ull;
+            cache_head = head && (v & 2u);
+        }
+        const unsigned m = __ballot_sync(kFull, cache_head);
+        if (m) {
+            uint32_t base = 0;
+            if ((threadIdx.x & 31u) == 0) base = atomicAdd(o.n_cache_runs, (uint32_t)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (cache_head) o.cache_heads[base + __popc(m & lanemask_lt())] = (uint32_t)i;
+        }
     }
 }
 
