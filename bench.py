@@ -527,7 +527,7 @@ def bench_w1_uniform(torch, h, init, update_frac, reps=3):
                        base={"cpu_threads": 1},
                        space={"modes": 3, "threads": [128, 256, 512], "blocks_per_sm": [0],
                               "lock_log2": [22, 24], "granules": [GRANULE],
-                              "ws_chunk_bytes": [16384], "reps": 2})
+                              "ws_chunk_bytes": [16384], "reps": 4})
     with h.Context(1 << LOG2W, GRANULE, dict({"cpu_threads": 1}, **tuned["config"])) as ctx:
         ctx.load(init)
         ms = []

@@ -1241,3 +1241,7 @@ int hetm_batch_poll(hetm_ctx *c, uint64_t batch_id, hetm_batch_result *out) {
 }
 
 }  // extern "C"
+
+namespace hetm {
+int ctx_open_rounds(const hetm_ctx *c) { return c->r_open; }
+}  // namespace hetm

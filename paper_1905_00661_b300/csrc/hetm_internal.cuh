@@ -250,6 +250,8 @@ cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_
                          const int *err);
 // the serving loop's transactions-per-round capacity
 uint64_t server_max_round_tx(const hetm_server *s);
+// rounds launched by hetm_round(ctx, NULL) and not yet collected
+int ctx_open_rounds(const hetm_ctx *c);
 cudaError_t launch_mark(const uint32_t *addr, const int32_t *vals, uint64_t n, int32_t *W,
                         uint64_t n_words, uint32_t *rs, uint32_t *filter, uint32_t gshift,
                         uint32_t *ws, uint32_t cshift, int *err, int blocks, cudaStream_t s);

@@ -64,6 +64,7 @@ struct hetm_server {
     hetm_server_config cfg{};
     cudaStream_t copy = nullptr;
     cudaStream_t main = nullptr;
+    cudaEvent_t rdone[2] = {nullptr, nullptr};  // end of a launched group's result copies
     std::mutex mu;
     std::condition_variable cv_in, cv_done;
     std::deque<Req *> waiting;
@@ -158,9 +159,13 @@ void finish(hetm_server *s, std::vector<Req *> &group, int rc) {
     s->cv_in.notify_all();
 }
 
+// rounds of the context launched and not yet collected
+int open_rounds(hetm_server *s) { return hetm::ctx_open_rounds(s->ctx); }
+bool round_opened(hetm_server *s) { return open_rounds(s) > 0; }
+
 // Launch one round for `group` (already staged): the executor waits for
 // the staging copies; result copies are queued behind the round.
-int launch_round(hetm_server *s, std::vector<Req *> &group) {
+int launch_round(hetm_server *s, std::vector<Req *> &group, cudaEvent_t done) {
     const hetm::Range range("hetm_server round");
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return HETM_ECUDA;
@@ -175,16 +180,19 @@ int launch_round(hetm_server *s, std::vector<Req *> &group) {
         const int c = collect(s, q);
         if (rc == HETM_OK) rc = c;
     }
+    // results of this group are in host memory once the stream passes here
+    if (cudaEventRecord(done, s->main) != cudaSuccess && rc == HETM_OK) rc = HETM_ECUDA;
     return rc;
 }
 
 // Wait for the round of `group` and complete its batches.
-void complete_round(hetm_server *s, std::vector<Req *> &group, int rc) {
+void complete_round(hetm_server *s, std::vector<Req *> &group, int rc, cudaEvent_t done) {
     hetm_round_stats st;
     std::memset(&st, 0, sizeof(st));
     const int w = hetm_round_wait(s->ctx, &st);
     if (rc == HETM_OK) rc = w;
-    if (cudaStreamSynchronize(s->main) != cudaSuccess && rc == HETM_OK) rc = HETM_ECUDA;
+    // this group's result copies only (the next round may already be queued)
+    if (cudaEventSynchronize(done) != cudaSuccess && rc == HETM_OK) rc = HETM_ECUDA;
     // every transaction commits unless the round reports give-ups, which
     // are attributed to the batches in order
     uint64_t left = st.committed;
@@ -229,34 +237,55 @@ int stage_group(hetm_server *s, std::vector<Req *> &group) {
     return rc;
 }
 
-// Pipeline: while round k runs on the GPU, round k+1's batches are admitted
-// and copied to the device.
+// Pipeline: while round k runs on the GPU, round k+1's batches are admitted,
+// copied to the device and launched behind it (two rounds in flight on the
+// context), so that the GPU goes from one round to the next without waiting
+// for the host to complete the first.
 void loop_main(hetm_server *s) {
-    std::vector<Req *> cur;
+    std::vector<Req *> cur;  // launched, not completed
+    int cur_rc = HETM_OK;
+    int ev = 0;  // s->rdone[ev]: the end of cur's result copies
     for (;;) {
-        if (cur.empty()) {
-            if (!admit(s, cur, true)) return;
-            if (cur.empty()) {
+        if (cur.empty()) {  // nothing in flight: wait for work
+            std::vector<Req *> g;
+            if (!admit(s, g, true)) return;
+            if (g.empty()) {
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
                 continue;
             }
-            const int rc = stage_group(s, cur);
+            const int rc = stage_group(s, g);
             if (rc != HETM_OK) {
-                finish(s, cur, rc);
-                cur.clear();
+                finish(s, g, rc);
                 continue;
             }
+            cur_rc = launch_round(s, g, s->rdone[ev]);
+            if (cur_rc != HETM_OK && !round_opened(s)) {
+                finish(s, g, cur_rc);  // nothing was launched
+                continue;
+            }
+            cur.swap(g);
         }
-        const int rc = launch_round(s, cur);
         std::vector<Req *> next;
+        int next_rc = HETM_OK;
         admit(s, next, false);
-        int rc_next = next.empty() ? HETM_OK : stage_group(s, next);
-        complete_round(s, cur, rc);
-        if (rc_next != HETM_OK) {
-            finish(s, next, rc_next);
-            next.clear();
+        bool next_open = false;
+        if (!next.empty()) {
+            next_rc = stage_group(s, next);
+            if (next_rc == HETM_OK) {
+                const int before = open_rounds(s);
+                next_rc = launch_round(s, next, s->rdone[ev ^ 1]);
+                next_open = open_rounds(s) > before;
+            }
         }
-        cur.swap(next);
+        complete_round(s, cur, cur_rc, s->rdone[ev]);
+        cur.clear();
+        if (next_open) {
+            cur.swap(next);
+            cur_rc = next_rc;
+            ev ^= 1;
+        } else if (!next.empty()) {
+            finish(s, next, next_rc);  // its round was never launched
+        }
     }
 }
 
@@ -294,7 +323,12 @@ int hetm_server_create(hetm_server **out, hetm_ctx *ctx, const hetm_server_confi
     }
     s->budget = d.device_budget ? d.device_budget : free_b / 2;
     s->main = static_cast<cudaStream_t>(hetm_ctx_stream(ctx));
-    if (cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->rdone[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->rdone[1], cudaEventDisableTiming) != cudaSuccess) {
+        if (s->copy) cudaStreamDestroy(s->copy);
+        for (auto e : s->rdone)
+            if (e) cudaEventDestroy(e);
         delete s;
         return HETM_ECUDA;
     }
@@ -387,6 +421,8 @@ void hetm_server_destroy(hetm_server *s) {
     if (s->loop.joinable()) s->loop.join();
     for (auto &kv : s->all) delete kv.second;
     if (s->copy) cudaStreamDestroy(s->copy);
+    for (auto e : s->rdone)
+        if (e) cudaEventDestroy(e);
     delete s;
 }
 
