@@ -34,8 +34,8 @@ def _overlay(state, log):
     state[log["addr"][order]] = log["value"][order]
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_two_rounds_in_flight_equal_two_rounds_in_sequence(hetm, torch, mode):
+@pytest.mark.parametrize("mode,early", [(0, 0), (1, 0), (0, 1)])
+def test_two_rounds_in_flight_equal_two_rounds_in_sequence(hetm, torch, mode, early):
     h = hetm
     start = wl.init_words(31, 0, N)
     txa = wl.rmw_batch(seed=31, batch=0, n_tx=20000, log2_words=LOG2W - 1)
@@ -43,7 +43,8 @@ def test_two_rounds_in_flight_equal_two_rounds_in_sequence(hetm, torch, mode):
     loga = np.concatenate(wl.cpu_write_log(31, 0, 3000, LOG2W - 1, cpu_threads=1, offset=N // 2))
     logb = np.concatenate(wl.cpu_write_log(31, 1, 2000, LOG2W - 1, cpu_threads=1, offset=N // 2))
     logb["ts"] += loga["ts"].max()
-    with h.Context(N, G, {"exec_mode": mode, "cpu_threads": 1, "ws_chunk_bytes": C}) as ctx:
+    cfg = {"exec_mode": mode, "cpu_threads": 1, "ws_chunk_bytes": C, "early_validate": early}
+    with h.Context(N, G, cfg) as ctx:
         ctx.load(start)
         boa = submit(ctx, torch, wl.WORKLOAD_RMW, txa)
         ctx.cpu_log_write(0, loga)
