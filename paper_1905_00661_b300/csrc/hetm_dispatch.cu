@@ -369,13 +369,18 @@ int hetm_dispatch_create(hetm_dispatch **out, hetm_server *server, hetm_gpu_batc
     d->cfg = c;
     int dev = -1;
     if (server && cudaGetDevice(&dev) != cudaSuccess) dev = -1;
-    for (uint32_t w = 0; w < c.cpu_workers; ++w) d->workers.emplace_back(cpu_worker, d, w);
-    d->ctl = std::thread(controller, d);
-    if (server)
-        d->cmp = std::thread([d, dev] {
-            if (dev >= 0) cudaSetDevice(dev);
-            completer(d);
-        });
+    try {
+        for (uint32_t w = 0; w < c.cpu_workers; ++w) d->workers.emplace_back(cpu_worker, d, w);
+        d->ctl = std::thread(controller, d);
+        if (server)
+            d->cmp = std::thread([d, dev] {
+                if (dev >= 0) cudaSetDevice(dev);
+                completer(d);
+            });
+    } catch (...) {  // a thread could not be started: stop the ones that were
+        hetm_dispatch_destroy(d);
+        return HETM_ENOMEM;
+    }
     *out = d;
     return HETM_OK;
 }

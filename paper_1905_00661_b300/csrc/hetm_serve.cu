@@ -334,10 +334,15 @@ int hetm_server_create(hetm_server **out, hetm_ctx *ctx, const hetm_server_confi
     }
     int dev = 0;
     cudaGetDevice(&dev);
-    s->loop = std::thread([s, dev] {
-        cudaSetDevice(dev);
-        loop_main(s);
-    });
+    try {
+        s->loop = std::thread([s, dev] {
+            cudaSetDevice(dev);
+            loop_main(s);
+        });
+    } catch (...) {
+        hetm_server_destroy(s);
+        return HETM_ENOMEM;
+    }
     *out = s;
     return HETM_OK;
 }
