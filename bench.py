@@ -818,7 +818,7 @@ def combine_ranks(torch, dist, device, ms, e2e_s, committed, e2e_commit):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--steps", type=int, default=16)  # the 16 rounds of the RMW configuration
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--serve-batches", type=int, default=300)
