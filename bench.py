@@ -570,7 +570,7 @@ def bench_cache(torch, h, n_batches=24, seed=6):
                  torch.empty(len(r), dtype=torch.uint8, device="cuda"),
                  torch.empty(len(r), dtype=torch.int64, device="cuda")) for r in reqs]
         ms = []
-        for rep in range(3):
+        for rep in range(6):  # the first is a warm-up; the median of five
             for d, r, (o, st_, out) in zip(dev, reqs, outs):
                 ctx.submit_batch(h.HETM_WL_CACHE, d, o, st_, out, n_tx=len(r))
             st = ctx.round(stats=True)
