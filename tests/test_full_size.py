@@ -1,4 +1,5 @@
-"""CUDA path vs the oracle at the validation-at-scale configuration's full size (needs a GPU).
+"""CUDA path vs the oracle at full size (needs a GPU): the validation-at-scale
+round, and the RMW round configuration's 4M-transaction batch.
 
 The benchmark's validation workload, unchanged: 2^28 STMR words (1 GiB) and its
 shadow, 64-byte granules (a 2 MiB RS_bmp), 5% of the granules read by the GPU
@@ -89,3 +90,34 @@ def test_round_full_size_final_state(hetm, torch, vr, variant):
         assert bool(st["conflict"]) == bool(ref.conflict)
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_W), ref.final)
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_S), ref.final)
+
+
+def test_executor_full_size_replay(hetm, torch):
+    """The RMW round configuration's batch at full size: 4M W1 transactions (10%
+    updates, 4 distinct Zipf(0.99) words each over the lower 2^27 words of a
+    2^28-word STMR), ordered executor in 512-transaction segments with 1 KiB
+    granules and 16 KiB chunks (the shape the benchmark times).  The oracle
+    replays the reported order: every committed transaction's sum, every word
+    of STMR^W, and RS_bmp / WS_bmp exactly."""
+    from roundkit import gpu_bitmaps, submit
+    h = hetm
+    g, c = 1024, 16384
+    start = wl.init_stmr(2, 1 << LOG2W)
+    tx = wl.rmw_batch(seed=2, batch=0, n_tx=1 << 22, log2_words=LOG2W - 1)
+    cfg = {"exec_mode": 0, "exec_threads": 512, "ws_chunk_bytes": c, "cpu_threads": 1}
+    with h.Context(1 << LOG2W, g, cfg) as ctx:
+        ctx.load(start)
+        bo = submit(ctx, torch, wl.WORKLOAD_RMW, tx)
+        ctx.gpu_exec()
+        ctx.sync()
+        torch.cuda.synchronize()
+        w = ctx.read_stmr(h.STMR_W)
+        rs_bits, ws_bits = gpu_bitmaps(ctx, h)
+        keys, stat, out = bo.host()
+    assert (stat == 1).all()
+    replayed = start.copy()
+    ref_out, R, D = oracle.replay_rmw(replayed, tx, keys, stat, g, c)
+    np.testing.assert_array_equal(out, ref_out)
+    np.testing.assert_array_equal(w, replayed)
+    np.testing.assert_array_equal(rs_bits, R)
+    np.testing.assert_array_equal(ws_bits, D)
