@@ -1,5 +1,6 @@
 """CUDA path vs the oracle at full size (needs a GPU): the validation-at-scale
-round, and the RMW round configuration's 4M-transaction batch.
+round, the RMW round configuration's 4M-transaction batch, and the object-cache
+configuration's 24 fused batches.
 
 The benchmark's validation workload, unchanged: 2^28 STMR words (1 GiB) and its
 shadow, 64-byte granules (a 2 MiB RS_bmp), 5% of the granules read by the GPU
@@ -117,6 +118,43 @@ def test_executor_full_size_replay(hetm, torch):
     assert (stat == 1).all()
     replayed = start.copy()
     ref_out, R, D = oracle.replay_rmw(replayed, tx, keys, stat, g, c)
+    np.testing.assert_array_equal(out, ref_out)
+    np.testing.assert_array_equal(w, replayed)
+    np.testing.assert_array_equal(rs_bits, R)
+    np.testing.assert_array_equal(ws_bits, D)
+
+
+def test_object_cache_full_size_replay(hetm, torch):
+    """The object-cache configuration at full size: 2^22 sets x 8 ways prefilled
+    with 2^25 keys, 24 uneven batches (1K-512K requests, log-uniform, 90% GET,
+    Zipf(0.99) over 2^26 keys) fused into one launch of the ordered executor.
+    The oracle replays the reported order: every result, the cache regions of
+    STMR^W, and RS_bmp / WS_bmp exactly."""
+    from roundkit import gpu_bitmaps, submit
+    h = hetm
+    lay = wl.CacheLayout(22)
+    start = wl.cache_prefill(lay, 1 << 25)
+    sizes = wl.log_uniform_sizes(6, wl.S.SIZE, 24, 1 << 10, 1 << 19)
+    reqs = [wl.cache_batch(6, i, int(n), 1 << 26) for i, n in enumerate(sizes)]
+    cfg = {"cache_log2_sets": 22, "cache_key_base": lay.key_base, "cache_val_base": lay.val_base,
+           "cache_lru_base": lay.gpu_lru_base, "cache_ver_base": lay.ver_base, "lock_shift": 4,
+           "cpu_threads": 1, "ws_chunk_bytes": 16384}
+    g, c = 64, 16384
+    with h.Context(lay.n_words, g, cfg) as ctx:
+        ctx.load(start)
+        bos = [submit(ctx, torch, wl.WORKLOAD_CACHE, r) for r in reqs]
+        ctx.gpu_exec()
+        ctx.sync()
+        torch.cuda.synchronize()
+        w = ctx.read_stmr(h.STMR_W)
+        rs_bits, ws_bits = gpu_bitmaps(ctx, h)
+        res = [b.host() for b in bos]
+    keys = np.concatenate([r[0] for r in res])
+    stat = np.concatenate([r[1] for r in res])
+    out = np.concatenate([r[2] for r in res]).view(np.uint64)
+    assert (stat == 1).all()
+    replayed = start.copy()
+    ref_out, R, D = oracle.replay_cache(replayed, lay, np.concatenate(reqs), keys, stat, g, c)
     np.testing.assert_array_equal(out, ref_out)
     np.testing.assert_array_equal(w, replayed)
     np.testing.assert_array_equal(rs_bits, R)
