@@ -1,6 +1,7 @@
 """CUDA path vs the oracle at full size (needs a GPU): the validation-at-scale
-round, the RMW round configuration's 4M-transaction batch, and the object-cache
-configuration's 24 fused batches.
+round, the RMW round configuration's 4M-transaction batch, the object-cache
+configuration's 24 fused batches, and a serving mix of the serving
+configuration's shapes.
 
 The benchmark's validation workload, unchanged: 2^28 STMR words (1 GiB) and its
 shadow, 64-byte granules (a 2 MiB RS_bmp), 5% of the granules read by the GPU
@@ -159,3 +160,59 @@ def test_object_cache_full_size_replay(hetm, torch):
     np.testing.assert_array_equal(w, replayed)
     np.testing.assert_array_equal(rs_bits, R)
     np.testing.assert_array_equal(ws_bits, D)
+
+
+def test_serving_mix_full_size(hetm, torch):
+    """The serving configuration's shapes at full size: one STMR holding the
+    object cache (2^22 sets) and 2^26 bank accounts, 12 batches of 1K-1M
+    transactions (log-uniform, bank or cache at random) submitted at once to
+    the serving loop, which fuses them into rounds.  Every bank transfer
+    commits and the accounts end at start + their net amounts (transfers
+    commute); the cache requests, replayed by the oracle in the reported
+    order, give every result and the final cache regions exactly."""
+    h = hetm
+    seed, n_batches, bank_log2 = 4, 12, 26
+    lay = wl.CacheLayout(22)
+    bank_base = (lay.n_words + 15) // 16 * 16
+    start = np.zeros(bank_base + (1 << bank_log2), np.int32)
+    start[:lay.n_words] = wl.cache_prefill(lay, 1 << 25)
+    start[bank_base:] = 1000
+    sizes = wl.log_uniform_sizes(seed, wl.S.SIZE, n_batches, 1 << 10, 1 << 20)
+    kinds = wl.uniform01(wl.draws_range(seed, wl.S.KIND, n_batches)) < 0.5
+    batches = [(1, wl.bank_transfers(seed * 1000 + i, (wl.S.SRC, wl.S.DST, wl.S.AMT), int(sizes[i]),
+                                     0, 1 << bank_log2)) if kinds[i]
+               else (3, wl.cache_batch(seed, i, int(sizes[i]), 1 << 26)) for i in range(n_batches)]
+    assert {k for k, _ in batches} == {1, 3}
+    cfg = {"cache_log2_sets": 22, "cache_key_base": lay.key_base, "cache_val_base": lay.val_base,
+           "cache_lru_base": lay.gpu_lru_base, "cache_ver_base": lay.ver_base, "lock_shift": 4,
+           "cpu_threads": 1}
+    with h.Context(len(start), 64, cfg) as ctx:
+        ctx.load(start)
+        with h.Server(ctx) as srv:
+            outs, ids = [], []
+            for wk, tx in batches:
+                o, s = np.zeros(len(tx), np.uint64), np.zeros(len(tx), np.uint8)
+                out = np.zeros(len(tx), np.uint64) if wk == 3 else None
+                ids.append(srv.submit(wk, tx, o, s, out, word_base=bank_base if wk == 1 else 0))
+                outs.append((o, s, out))
+            for i in ids:
+                srv.wait(i)
+        final = ctx.read_stmr(h.STMR_W)
+        np.testing.assert_array_equal(final, ctx.read_stmr(h.STMR_S))
+    bank = [(tx, o) for (wk, tx), o in zip(batches, outs) if wk == 1]
+    expect = start[bank_base:].astype(np.int64)
+    for tx, (o, s, _) in bank:
+        assert (s == 1).all()
+        np.add.at(expect, tx["src"], -tx["amount"].astype(np.int64))
+        np.add.at(expect, tx["dst"], tx["amount"].astype(np.int64))
+    np.testing.assert_array_equal(final[bank_base:], expect.astype(np.int32))
+    cache = [(tx, o) for (wk, tx), o in zip(batches, outs) if wk == 3]
+    reqs = np.concatenate([tx for tx, _ in cache])
+    keys = np.concatenate([o[0] for _, o in cache])
+    stat = np.concatenate([o[1] for _, o in cache])
+    got = np.concatenate([o[2] for _, o in cache])
+    assert (stat == 1).all()
+    rep = start[:lay.n_words].copy()
+    ref_out, _, _ = oracle.replay_cache(rep, lay, reqs, keys, stat, 64, 16384)
+    np.testing.assert_array_equal(got, ref_out)
+    np.testing.assert_array_equal(final[:lay.n_words], rep)
