@@ -537,7 +537,7 @@ void hetm_destroy(hetm_ctx *c) {
         if (g) cudaGraphExecDestroy(g);
     for (auto &slot : c->ev)
         for (auto &e : slot)
-        if (e) cudaEventDestroy(e);
+            if (e) cudaEventDestroy(e);
     for (auto &s : c->stage) {
         if (s.rounds) cudaFreeHost(s.rounds);
         if (s.batches) cudaFreeHost(s.batches);
