@@ -94,19 +94,22 @@ def test_round_full_size_final_state(hetm, torch, vr, variant):
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_S), ref.final)
 
 
-def test_executor_full_size_replay(hetm, torch):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_executor_full_size_replay(hetm, torch, mode):
     """The RMW round configuration's batch at full size: 4M W1 transactions (10%
     updates, 4 distinct Zipf(0.99) words each over the lower 2^27 words of a
-    2^28-word STMR), ordered executor in 512-transaction segments with 1 KiB
-    granules and 16 KiB chunks (the shape the benchmark times).  The oracle
-    replays the reported order: every committed transaction's sum, every word
-    of STMR^W, and RS_bmp / WS_bmp exactly."""
+    2^28-word STMR) with 1 KiB granules and 16 KiB chunks: the ordered executor
+    in 512-transaction segments (the shape the benchmark times) and the
+    optimistic STM (256-thread CTAs; the hot words make it retry a lot).  The
+    oracle replays the reported order: every committed transaction's sum,
+    every word of STMR^W, and RS_bmp / WS_bmp exactly."""
     from roundkit import gpu_bitmaps, submit
     h = hetm
     g, c = 1024, 16384
     start = wl.init_stmr(2, 1 << LOG2W)
     tx = wl.rmw_batch(seed=2, batch=0, n_tx=1 << 22, log2_words=LOG2W - 1)
-    cfg = {"exec_mode": 0, "exec_threads": 512, "ws_chunk_bytes": c, "cpu_threads": 1}
+    cfg = {"exec_mode": mode, "exec_threads": 512 if mode == 0 else 256, "ws_chunk_bytes": c,
+           "cpu_threads": 1}
     with h.Context(1 << LOG2W, g, cfg) as ctx:
         ctx.load(start)
         bo = submit(ctx, torch, wl.WORKLOAD_RMW, tx)
@@ -116,10 +119,14 @@ def test_executor_full_size_replay(hetm, torch):
         w = ctx.read_stmr(h.STMR_W)
         rs_bits, ws_bits = gpu_bitmaps(ctx, h)
         keys, stat, out = bo.host()
-    assert (stat == 1).all()
+    if mode == 0:
+        assert (stat == 1).all()  # the ordered executor never aborts
+    else:  # the STM's bounded retries may give some up: they must leave no trace
+        assert np.isin(stat, [1, 2]).all() and (stat == 1).mean() > 0.9
     replayed = start.copy()
     ref_out, R, D = oracle.replay_rmw(replayed, tx, keys, stat, g, c)
-    np.testing.assert_array_equal(out, ref_out)
+    ok = stat == 1
+    np.testing.assert_array_equal(out[ok], ref_out[ok])
     np.testing.assert_array_equal(w, replayed)
     np.testing.assert_array_equal(rs_bits, R)
     np.testing.assert_array_equal(ws_bits, D)
