@@ -94,20 +94,23 @@ def test_round_full_size_final_state(hetm, torch, vr, variant):
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_S), ref.final)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_executor_full_size_replay(hetm, torch, mode):
+@pytest.mark.parametrize("mode,uniform", [(0, False), (1, False), (1, True)])
+def test_executor_full_size_replay(hetm, torch, mode, uniform):
     """The RMW round configuration's batch at full size: 4M W1 transactions (10%
     updates, 4 distinct Zipf(0.99) words each over the lower 2^27 words of a
     2^28-word STMR) with 1 KiB granules and 16 KiB chunks: the ordered executor
     in 512-transaction segments (the shape the benchmark times) and the
-    optimistic STM (256-thread CTAs; the hot words make it retry a lot).  The
+    optimistic STM (256-thread CTAs; the hot words make it retry a lot), and
+    the W1-uniform batch under the STM (its read-only phase lists the updates
+    it leaves; Sec. V-A's W1, uniform words over the whole STMR).  The
     oracle replays the reported order: every committed transaction's sum,
     every word of STMR^W, and RS_bmp / WS_bmp exactly."""
     from roundkit import gpu_bitmaps, submit
     h = hetm
     g, c = 1024, 16384
     start = wl.init_stmr(2, 1 << LOG2W)
-    tx = wl.rmw_batch(seed=2, batch=0, n_tx=1 << 22, log2_words=LOG2W - 1)
+    tx = (wl.rmw_batch(seed=2, batch=7, n_tx=1 << 22, log2_words=LOG2W, uniform=True) if uniform
+          else wl.rmw_batch(seed=2, batch=0, n_tx=1 << 22, log2_words=LOG2W - 1))
     cfg = {"exec_mode": mode, "exec_threads": 512 if mode == 0 else 256, "ws_chunk_bytes": c,
            "cpu_threads": 1}
     with h.Context(1 << LOG2W, g, cfg) as ctx:
