@@ -161,17 +161,24 @@ def bench_ours(args, rank, world, local_rank, inputs):
     n_upd = [int(b["flags"].sum()) for b in batches]
     torch.cuda.synchronize()
 
-    def one_round(r):
+    def launch_round(r):
         b = r % len(batches)
         o, st_, out = outs[b]
         ctx.log_attach(dev_logs[r])
         ctx.submit_batch(h.HETM_WL_RMW, dev_tx[b], o, st_, out, txid_base=(r * N_TX) & 0xFFFFFFFF,
                          n_tx=N_TX)
-        st = ctx.round(stats=True)
+        ctx.round(stats=False)
+
+    def collect_round(r):
+        st = ctx.round_wait()
         if st["rc"] != h.HETM_OK:
             raise RuntimeError(f"round failed: {st}")
-        st["n_upd"] = n_upd[b]
+        st["n_upd"] = n_upd[r % len(batches)]
         return st
+
+    def one_round(r):
+        launch_round(r)
+        return collect_round(r)
 
     def barrier():
         torch.cuda.synchronize()
@@ -185,9 +192,14 @@ def bench_ours(args, rank, world, local_rank, inputs):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
     with Clocks(local_rank) as clk:
+        # two rounds in flight: round r+1 is queued on the device behind round
+        # r before the host collects round r (its batch and log pool slot differ)
         ev0.record(s)
+        launch_round(W)
         for r in range(W, W + K):
-            stats.append(one_round(r))
+            if r + 1 < W + K:
+                launch_round(r + 1)
+            stats.append(collect_round(r))
         ev1.record(s)
         barrier()
     ms = ev0.elapsed_time(ev1)
