@@ -523,35 +523,49 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
         if (d.status) d.status[li] = kCommitted;
         return true;
     };
-    // the indices left to the STM are appended block by block (one atomic per
-    // block and iteration: a counter per warp would serialize 1 in 32 of all
-    // transactions on one word); the trip count is uniform over the block so
-    // that its barriers are
-    __shared__ uint32_t warp_off[2][8];
-    __shared__ unsigned long long blk_base[2];
-    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    uint32_t it = 0;
-    for (uint64_t ub = blockIdx.x * (uint64_t)blockDim.x; ub < total; ub += stride, it ^= 1u) {
-        const uint64_t u = ub + threadIdx.x;
+    // The indices left to the STM are gathered in shared memory (one shared
+    // atomic per warp and iteration) and appended to the list with one global
+    // atomic per block at the end: one counter for the whole launch would
+    // serialize the appends.  What does not fit the block's buffer goes to
+    // the list directly, one atomic per warp.
+    constexpr uint32_t kCap = 4096;
+    __shared__ uint32_t s_list[kCap];
+    __shared__ uint32_t s_n;
+    __shared__ unsigned long long s_base;
+    const unsigned lane = threadIdx.x & 31u;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    // loop bound rounded up to whole warps so that the warp collectives are convergent
+    const uint64_t span = (total + 31) & ~31ull;
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < span; u += stride) {
         const bool ran = u < total && run_ro(u);
         n_commit += ran ? 1u : 0u;
         if (listing) {
             const bool left = u < total && !ran;
             const unsigned m = __ballot_sync(kFull, left);
-            if (lane == 0) warp_off[it][wid] = __popc(m);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                uint32_t sum = 0;
-                for (uint32_t w = 0; w < (blockDim.x >> 5); ++w) {
-                    const uint32_t c = warp_off[it][w];
-                    warp_off[it][w] = sum;
-                    sum += c;
+            if (m) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(&s_n, (uint32_t)__popc(m));
+                base = __shfl_sync(kFull, base, 0);
+                const uint32_t pos = base + __popc(m & lanemask_lt());
+                const bool spill = left && pos >= kCap;
+                if (left && !spill) s_list[pos] = (uint32_t)u;
+                const unsigned ms = __ballot_sync(kFull, spill);
+                if (ms) {
+                    unsigned long long g = 0;
+                    if (lane == (unsigned)(__ffs(ms) - 1)) g = atomicAdd(a.rest_n, (unsigned long long)__popc(ms));
+                    g = __shfl_sync(kFull, g, __ffs(ms) - 1);
+                    if (spill) a.rest[g + __popc(ms & lanemask_lt())] = (uint32_t)u;
                 }
-                blk_base[it] = sum ? atomicAdd(a.rest_n, (unsigned long long)sum) : 0ull;
             }
-            __syncthreads();
-            if (left) a.rest[blk_base[it] + warp_off[it][wid] + __popc(m & lanemask_lt())] = (uint32_t)u;
         }
+    }
+    __syncthreads();
+    if (listing) {
+        const uint32_t n = min(s_n, kCap);
+        if (threadIdx.x == 0) s_base = n ? atomicAdd(a.rest_n, (unsigned long long)n) : 0ull;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) a.rest[s_base + i] = s_list[i];
     }
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1) n_commit += __shfl_xor_sync(kFull, n_commit, w);
