@@ -108,6 +108,61 @@ def test_golden_cache(name):
     assert R.tolist() == ex["R"] and D.tolist() == ex["D"]
 
 
+def test_golden_cache_sets():
+    """Sec. V-D object cache over four sets: the set index is the SplitMix64
+    finalizer of the key (worked by hand in the golden), so a dropped hash,
+    a wrong shift or constant puts a key in the wrong set and fails here."""
+    g = _golden("cache_sets.json")
+    layout = wl.CacheLayout(log2_sets=g["log2_sets"])
+    assert layout.n_words == 196
+    img = np.zeros(layout.n_words, np.int32)
+    kw = img[layout.key_base:layout.val_base].view(np.uint64).reshape(4, 8)
+    vw = img[layout.val_base:layout.gpu_lru_base].view(np.uint64).reshape(4, 8)
+    for s_, (ks, vs) in enumerate(zip(g["start"]["keys"], g["start"]["values"])):
+        kw[s_, :len(ks)] = ks
+        vw[s_, :len(vs)] = vs
+    reqs = np.zeros(len(g["reqs"]), wl.CACHE_DTYPE)
+    for i, (k, v, op) in enumerate(g["reqs"]):
+        reqs[i]["key"], reqs[i]["value"], reqs[i]["op"] = k, v, op
+    out, R, D = oracle.replay_cache(img, layout, reqs, g["order"], g["status"],
+                                    g["granule_bytes"], g["chunk_bytes"])
+    ex = g["expect"]
+    assert out.tolist() == ex["out"]
+    assert kw.tolist() == ex["keys"]
+    assert vw.tolist() == ex["values"]
+    lru = img[layout.gpu_lru_base:layout.cpu_lru_base].reshape(4, 8)
+    assert lru.tolist() == ex["gpu_lru"]
+    assert img[layout.ver_base:layout.ver_base + 4].tolist() == ex["version"]
+    assert img[layout.cpu_lru_base:layout.ver_base].tolist() == [0] * 32
+    assert R.tolist() == ex["R"] and D.tolist() == ex["D"]
+
+
+def test_cache_replay_finds_every_prefilled_key():
+    """The prefill places keys by workloads.mix64 (pinned to published
+    SplitMix64 outputs); a GET of every placed key through the oracle's own
+    set index must hit and return the prefill's value (key * 3) on 256 sets."""
+    layout = wl.CacheLayout(log2_sets=8)
+    n_keys = 1024
+    img = wl.cache_prefill(layout, n_keys)
+    keys = np.arange(1, n_keys + 1, dtype=np.uint64)
+    placed = np.isin(keys, img[layout.key_base:layout.val_base].view(np.uint64))
+    assert placed.sum() > 0.95 * n_keys          # ~4 keys a set: few sets overflow
+    reqs = np.zeros(int(placed.sum()), wl.CACHE_DTYPE)
+    reqs["key"] = keys[placed]
+    order = np.arange(1, reqs.size + 1, dtype=np.uint64) * 2
+    out, _, _ = oracle.replay_cache(img.copy(), layout, reqs, order, np.ones(reqs.size, np.uint8),
+                                    64, 64)
+    np.testing.assert_array_equal(out, keys[placed] * np.uint64(3))
+    # the keys the prefill could not place (full sets) miss
+    missed = np.zeros(int((~placed).sum()), wl.CACHE_DTYPE)
+    missed["key"] = keys[~placed]
+    if missed.size:
+        out, _, _ = oracle.replay_cache(img.copy(), layout, missed,
+                                        np.arange(1, missed.size + 1, dtype=np.uint64) * 2 + 1,
+                                        np.ones(missed.size, np.uint8), 64, 64)
+        assert (out == np.uint64(2**64 - 1)).all()
+
+
 # ---------------------------------------------------------------------------
 # closed-form special cases (Sec. IV-C)
 # ---------------------------------------------------------------------------
