@@ -903,8 +903,7 @@ int hetm_exec_counters(hetm_ctx *c, uint64_t *committed, uint64_t *gave_up, uint
     if (aborts) *aborts = h[2];
     int err = 0;
     CK(cudaMemcpy(&err, &c->scr->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err == kErrTimeout) return HETM_ETIMEOUT;
-    return err ? HETM_EDEVICE : HETM_OK;
+    return err_code(err);
 }
 
 int hetm_gpu_mark(hetm_ctx *c, const uint32_t *addr, const int32_t *vals, uint64_t n) {
@@ -973,7 +972,7 @@ int hetm_validate(hetm_ctx *c, uint64_t *n_conflicts, uint32_t *dev_flag_bits) {
         h = c->out->conflicts;
         err = c->out->err;
         *n_conflicts = h;
-        if (err) return err == kErrTimeout ? HETM_ETIMEOUT : HETM_EDEVICE;
+        if (err) return err_code(err);
     }
     return HETM_OK;
 }
@@ -1167,7 +1166,7 @@ int hetm_round_wait(hetm_ctx *c, hetm_round_stats *stats) {
     stats->n_log = n;
     stats->n_conflicts = out->conflicts;
     stats->conflict = out->conflicts != 0;
-    stats->err = out->err == 0 ? HETM_OK : (out->err == kErrTimeout ? HETM_ETIMEOUT : HETM_EDEVICE);
+    stats->err = err_code(out->err);
     stats->committed = out->counters[0] - c->prev_counters[0];
     stats->gave_up = out->counters[1] - c->prev_counters[1];
     stats->aborts = out->counters[2] - c->prev_counters[2];

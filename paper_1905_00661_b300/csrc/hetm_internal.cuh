@@ -45,9 +45,17 @@ struct DevRound {
     uint32_t pad;
 };
 
-// Device error word values (first error wins).
+// Device error word: a set of bits, each site ORs its own in, so that no
+// error hides another (a timeout must still undo the batch after an address
+// error of the same or an earlier round).
 constexpr int kErrAddr = 1;
 constexpr int kErrTimeout = 2;
+
+// HETM_ETIMEOUT when the execution phase ran out of its budget (whatever else
+// went wrong), HETM_EDEVICE for any other device error, else HETM_OK.
+inline int err_code(int bits) {
+    return (bits & kErrTimeout) ? HETM_ETIMEOUT : (bits ? HETM_EDEVICE : HETM_OK);
+}
 
 // Arguments of the executor kernel.
 struct ExecArgs {
@@ -175,8 +183,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-__device__ __forceinline__ void set_err(int *err, int code) {
-    if (err) atomicCAS(err, 0, code);
+__device__ __forceinline__ void set_err(int *err, int bit) {
+    if (err && !(*(volatile int *)err & bit)) atomicOr(err, bit);
 }
 
 // SplitMix64 finalizer (Steele, Lea & Flood 2014): the cache's set hash.

@@ -13,9 +13,10 @@
 // Scratch: one partial hit count and one error flag per block, in a static
 // __device__ array that every GPU loading this library holds until the
 // process exits.  Each block handles a fixed 8192-tuple span and writes its
-// own slot; a one-block finalize kernel sums the slots in block order, so
-// the count is deterministic.  The span and slot count bound the input to
-// HETM_NOALLOC_MAX_TUPLES tuples.
+// own slot; a one-block finalize kernel adds the slots up.  The count is an
+// integer sum, so it does not depend on the order in which the slots are
+// added.  The span and slot count bound the input to HETM_NOALLOC_MAX_TUPLES
+// tuples.
 
 #include <mutex>
 
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(256) k_validate_noalloc(const hetm_log_entry *
     }
 }
 
-// Sum the first n_blocks slots in block order into the caller's outputs.
+// Add up the first n_blocks slots into the caller's outputs (integer sums
+// and ORs: the result does not depend on the order of the additions).
 __global__ void __launch_bounds__(1024) k_noalloc_finish(const NoAllocScratch *scr,
                                                          uint32_t n_blocks,
                                                          unsigned long long *count, int *err) {
@@ -155,10 +157,9 @@ int scratch_for_current_device(NoAllocScratch **out) {
     std::lock_guard<std::mutex> g(g_sym_mu);
     if (!g_sym_ptr[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return HETM_ECUDA;
-        }
+        // the lookup's own return code decides; an error some earlier call
+        // left pending on this thread is neither read nor cleared here
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HETM_ECUDA;
         g_sym_ptr[dev] = p;
     }
     *out = static_cast<NoAllocScratch *>(g_sym_ptr[dev]);
@@ -184,12 +185,21 @@ extern "C" int hetm_validate_noalloc(const hetm_log_entry *dev_log, uint64_t n,
     uint32_t gshift = 0;
     while ((4u << gshift) < granule_bytes) ++gshift;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const uint32_t blocks = (uint32_t)((n + kSpan - 1) / kSpan);
-    if (blocks)
-        k_validate_noalloc<<<blocks, 256, 0, s>>>(dev_log, n, dev_rs_bmp, gshift, stmr_words,
-                                                  dev_flag_bits, scr);
-    k_noalloc_finish<<<1, 1024, 0, s>>>(scr, blocks,
-                                        reinterpret_cast<unsigned long long *>(dev_n_conflicts),
-                                        dev_err);
-    return cudaGetLastError() == cudaSuccess ? HETM_OK : HETM_ECUDA;
+    uint32_t blocks = (uint32_t)((n + kSpan - 1) / kSpan);
+    // Each launch is checked by its own return code, so that only a failure
+    // of this call's launches maps to HETM_ECUDA (an error an unrelated
+    // earlier call left pending on this thread is neither reported nor
+    // cleared).
+    if (blocks) {
+        void *args[] = {&dev_log, &n, &dev_rs_bmp, &gshift, &stmr_words, &dev_flag_bits, &scr};
+        if (cudaLaunchKernel((const void *)k_validate_noalloc, dim3(blocks), dim3(256), args, 0, s) !=
+            cudaSuccess)
+            return HETM_ECUDA;
+    }
+    unsigned long long *count = reinterpret_cast<unsigned long long *>(dev_n_conflicts);
+    const NoAllocScratch *cscr = scr;
+    void *fargs[] = {&cscr, &blocks, &count, &dev_err};
+    if (cudaLaunchKernel((const void *)k_noalloc_finish, dim3(1), dim3(1024), fargs, 0, s) != cudaSuccess)
+        return HETM_ECUDA;
+    return HETM_OK;
 }

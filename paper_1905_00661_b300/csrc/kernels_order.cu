@@ -1341,19 +1341,29 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
         e0 = cudaEventRecord(join, side);
         if (e0 != cudaSuccess) return e0;
     }
+    // Every return from here on first joins the side stream back into s, so
+    // that a failure during a stream capture ends the capture with its own
+    // error instead of an unjoined fork.
+    auto joined = [&](cudaError_t err) -> cudaError_t {
+        if (beside) {
+            const cudaError_t ej = cudaStreamWaitEvent(s, join, 0);
+            if (err == cudaSuccess) err = ej;
+        }
+        return err;
+    };
     const uint32_t scan_grid = (o.cap_tx + kScanTile - 1) / kScanTile;
     cudaError_t e = device_scan<SumOp, true>(o.cnt, o.cnt, o.n_tx32, 0, scan_grid, o.scan_tot, 0, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return joined(e);
     k_ord_emit<<<stream_blocks, 256, 0, s>>>(o);
     e = radix_sort(o.keys0, o.vals0, o.keys1, o.vals1, o.n_acc, o.cap_acc, o.key_bits, o.hist,
                    o.scan_tot, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return joined(e);
     k_ord_runs<<<stream_blocks, 256, 0, s>>>(o);
     const uint32_t acc_grid = (o.cap_acc + kScanTile - 1) / kScanTile;
     e = device_scan<PairMaxOp, false>(o.runs, o.runs, o.n_acc, 0, acc_grid, o.scan_tot, 0, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return joined(e);
     k_ord_acc<<<stream_blocks, 256, 0, s>>>(o);
-    if (beside) e = cudaStreamWaitEvent(s, join, 0);
+    if (beside) e = joined(cudaSuccess);
     else k_ord_ro<<<stream_blocks, 256, 0, s>>>(o);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(o.e.next, 0, sizeof(unsigned long long), s);

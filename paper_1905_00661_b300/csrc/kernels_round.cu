@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256) k_merge(const uint32_t *__restrict__ ws, 
     // an execution phase that ran out of its time budget is undone like a
     // batch that lost a conflict (its transactions ran only in part)
     const bool conflict =
-        (err && *err == kErrTimeout) || (force >= 0 ? force != 0 : (*conflicts != 0ull));
+        (err && (*err & kErrTimeout)) || (force >= 0 ? force != 0 : (*conflicts != 0ull));
     const uint4 *src = reinterpret_cast<const uint4 *>(conflict ? S : W);
     uint4 *dst = reinterpret_cast<uint4 *>(conflict ? W : S);
     const unsigned lane = threadIdx.x & 31u;

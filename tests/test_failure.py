@@ -8,6 +8,12 @@
   == the start state with the CPU log applied (Sec. IV-C conflict case).  The
   error stays until hetm_load; after it the same context runs a short batch
   to the oracle's result.
+* A timeout after an address error: one transaction of the batch names a word
+  out of range (the device error word records it before the executor runs),
+  or an earlier round on the same context left that error standing.  The
+  timeout must still be reported and the batch undone, since a partly
+  executed batch must never be merged as committed (Sec. IV-C merge phase,
+  Sec. IV-D rollback).
 * Allocation failure in hetm_init (the device allocator hook refuses the k-th
   request): HETM_ENOMEM, and every buffer it got is given back.
 """
@@ -79,6 +85,56 @@ def test_execution_budget_runs_out_and_the_batch_is_undone(hetm, torch, mode):
         ref_out, _, _ = oracle.replay_rmw(replayed, small, keys, stat, G, C)
         np.testing.assert_array_equal(out, ref_out)
         np.testing.assert_array_equal(ctx.read_stmr(h.STMR_W), replayed)
+
+
+def _chain_round(h, ctx, torch, start, bad_tx, seed=23):
+    """One round whose execution phase runs out of its 200 us budget; bad_tx
+    puts one out-of-range word into the batch."""
+    tx = wl.rmw_batch(seed=seed, batch=0, n_tx=200000, log2_words=LOG2W - 1, update_frac=1.0)
+    if bad_tx:
+        tx["addr"][777, 2] = N + 5
+    log = np.concatenate(wl.cpu_write_log(seed, 0, 2000, LOG2W - 1, cpu_threads=1, offset=N // 2))
+    bo = submit(ctx, torch, wl.WORKLOAD_RMW, tx)
+    ctx.cpu_log_write(0, log)
+    st = ctx.round(stats=True)
+    return st, bo, log
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("where", ["same_batch", "earlier_round"])
+def test_timeout_after_an_address_error_still_undoes_the_batch(hetm, torch, mode, where):
+    h = hetm
+    start = wl.init_words(29, 0, N)
+    cfg = {"exec_mode": mode, "exec_budget_us": 200, "cpu_threads": 1, "ws_chunk_bytes": C,
+           "max_round_tx": 1 << 18}
+    with h.Context(N, G, cfg) as ctx:
+        ctx.load(start)
+        ts_state = np.zeros(N, np.uint32)
+        if where == "earlier_round":
+            # a short clean round whose only fault is one out-of-range word
+            small = wl.rmw_batch(seed=30, batch=0, n_tx=256, log2_words=LOG2W, uniform=True)
+            small["addr"][5, 0] = N + 1
+            bo = submit(ctx, torch, wl.WORKLOAD_RMW, small)
+            st = ctx.round(stats=True)
+            assert st["rc"] == h.HETM_EDEVICE
+            assert st["outcome"] == h.HETM_OUTCOME_CLEAN
+            keys, stat, _ = bo.host()
+            assert stat[5] == 2 and (np.delete(stat, 5) == 1).all()
+            replayed = start.copy()
+            oracle.replay_rmw(replayed, small, keys, stat, G, C)
+            np.testing.assert_array_equal(ctx.read_stmr(h.STMR_W), replayed)
+            start = replayed
+        st, bo, log = _chain_round(h, ctx, torch, start, bad_tx=where == "same_batch")
+        assert st["rc"] == h.HETM_ETIMEOUT
+        assert st["outcome"] == h.HETM_OUTCOME_GPU_ROLLED_BACK
+        _, stat, _ = bo.host()
+        assert np.isin(stat, [1, 2]).all() and st["gave_up"] > 0
+        # the rolled-back round's final state is the oracle's conflict case
+        expect, ties = oracle.final_state(start, start, True, log, ts_state.copy())
+        assert ties == 0
+        np.testing.assert_array_equal(ctx.read_stmr(h.STMR_W), expect)
+        np.testing.assert_array_equal(ctx.read_stmr(h.STMR_S), expect)
+        assert ctx.exec_counters()["rc"] == h.HETM_ETIMEOUT
 
 
 @pytest.mark.parametrize("fail_at", [0, 3, 9])

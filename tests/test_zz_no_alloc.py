@@ -1,4 +1,4 @@
-"""hetm_validate_noalloc against hetm_validate_only.
+"""hetm_validate_noalloc against hetm_validate_only and the oracle.
 
 The allocation-free entry point serves callers that cannot allocate device
 memory when they validate -- work being captured into a CUDA graph, serving
@@ -7,13 +7,18 @@ whose host framework owns all device memory.  It keeps its scratch in one
 static device array shared by every call, so the check runs two calls in a
 row (a large log, then a shorter one that must not see the first call's
 leftovers) and compares flags, hit count and status with the context-based
-entry point on the same inputs.  Integer results: they must match exactly.
+entry point on the same inputs, and the flags and count with the oracle's
+brute-force set intersection.  Further cases: out-of-range tuples (reported
+as HETM_EDEVICE and left out of the count), no flag output, an empty log,
+and logs shorter than one 128-tuple tile.  Integer results: they must match
+exactly.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads as wl
 from roundkit import flags_of, to_dev
 
@@ -57,5 +62,53 @@ def test_noalloc_matches_validate_only_on_two_calls(hetm):
             got = flags_of(flags.cpu().numpy().view(np.uint32), n)
             exp = flags_of(ref_flags.cpu().numpy().view(np.uint32), n)
             np.testing.assert_array_equal(got, exp)
+            o_flags, o_n = oracle.conflicts(v.log[:n], v.read_granules, v.granule_bytes)
+            np.testing.assert_array_equal(got, o_flags)
+            assert int(cnt.item()) == o_n
         # the planted recipe fixes the hit count of the full log
-        assert int(ref_cnt.item()) > 0
+        assert int(ref_cnt.item()) == v.n_hits_planted
+
+
+@pytest.mark.gpu
+def test_noalloc_edge_cases(hetm):
+    import torch
+    h = hetm
+    n_words, G = 1 << 16, 64
+    v = wl.validation_round(seed=13, log2_words=16, granule_bytes=G, n_log=4099, with_init=False)
+    log = v.log.copy()
+    bad = np.array([3, 64, 200, 4098])
+    log["addr"][bad] = n_words + np.arange(bad.size, dtype=np.uint32)
+    with h.Context(n_words, G) as ctx:
+        first = (v.read_granules.astype(np.uint64) * (G // 4)).astype(np.uint32)
+        ctx.gpu_mark(torch.from_numpy(first).cuda())
+        rs = ctx.device_tensor(h.RS_BMP)
+        stream = ctx.stream
+        for n in (0, 1, 31, 127, 128, 129, len(log)):
+            part = log[:n]
+            dlog = to_dev(torch, part)
+            words = max((n + 31) // 32, 1)
+            flags = torch.full((words,), -1, dtype=torch.int32, device="cuda")
+            cnt = torch.full((1,), 777, dtype=torch.int64, device="cuda")
+            err = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+            for with_flags in (True, False):
+                torch.cuda.synchronize()
+                rc = h.hetm_validate_noalloc(dlog, n, rs, G, n_words, flags if with_flags else None,
+                                             cnt, err, stream.cuda_stream)
+                assert rc == h.HETM_OK
+                stream.synchronize()
+                o_flags, o_n = oracle.conflicts(part, v.read_granules, G)
+                assert int(cnt.item()) == o_n
+                n_bad = int((part["addr"] >= n_words).sum())
+                assert int(err.item()) == (h.HETM_EDEVICE if n_bad else h.HETM_OK)
+                if with_flags and n:
+                    got = flags_of(flags.cpu().numpy().view(np.uint32), n)
+                    np.testing.assert_array_equal(got, o_flags)
+            if n and n_bad:
+                # the context-based entry point reports the same tuples
+                ref_flags = torch.zeros(words, dtype=torch.int32, device="cuda")
+                ref_cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+                ctx.validate_only(dlog, n, ref_flags, ref_cnt)
+                assert ctx.exec_counters()["rc"] == h.HETM_EDEVICE
+                assert int(ref_cnt.item()) == o_n
+                np.testing.assert_array_equal(
+                    flags_of(ref_flags.cpu().numpy().view(np.uint32), n), o_flags)
