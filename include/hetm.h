@@ -75,6 +75,7 @@ typedef struct hetm_log_entry {
 #define HETM_WL_BANK 1  /* hetm_bank_tx                      */
 #define HETM_WL_RMW 2   /* hetm_rmw_tx (W1 of Sec. V-A)       */
 #define HETM_WL_CACHE 3 /* hetm_cache_req (Sec. V-D)          */
+#define HETM_WL_W2 4    /* hetm_w2_tx (W2 of Sec. V-A)        */
 
 /* bank transfer: bal[src] -= amount; bal[dst] += amount (int32, wrapping).
  * Accounts are words base+src, base+dst with base = hetm_batch.word_base. */
@@ -90,6 +91,20 @@ typedef struct hetm_rmw_tx {
     uint32_t addr[4];
     uint32_t flags;
 } hetm_rmw_tx;
+
+/* W2 of Sec. V-A: like W1, but every transaction reads 40 words.  A
+ * read-only transaction outputs the 32-bit sum s of its 40 words; with flags
+ * bit 0 set it also writes s + j + txid to its j-th word for j = 0..3 (the
+ * update transactions of both workloads update 4 positions).  The 40 words
+ * of one transaction must be distinct.  176 bytes (16-byte multiple).
+ * W2 runs under HETM_EXEC_OPTIMISTIC (read-only transactions in its
+ * read-only phase, updates under the STM with validated reads); a context
+ * in ordered mode refuses W2 batches (HETM_EINVAL at submission). */
+typedef struct hetm_w2_tx {
+    uint32_t addr[40];
+    uint32_t flags;
+    uint32_t pad[3];
+} hetm_w2_tx;
 
 /* Object-cache request, op 0 = GET, 1 = PUT.  Set = SplitMix64 finalizer of
  * key mod 2^cache_log2_sets.  GET hit: out = value and the GPU LRU stamp of
@@ -173,6 +188,12 @@ typedef struct hetm_config {
      * its merge undoes the whole batch (S -> W), as after a lost conflict.
      * The error stays reported until hetm_load. */
     uint32_t exec_budget_us;
+    /* 1: the executors record nothing in RS_bmp / WS_bmp.  Only for measuring
+     * what the GPU instrumentation costs (Sec. V-A compares against the
+     * uninstrumented GPU TM): validation then cannot see the batch's reads
+     * and the merge moves no chunk, so a round's result is not SHeTM's.
+     * 0 (default): instrumented. */
+    uint32_t uninstrumented;
 } hetm_config;
 
 #define HETM_POLICY_GPU_LOSES 0
@@ -234,8 +255,8 @@ typedef struct hetm_batch {
     const void *tx;      /* n_tx records of the workload's type            */
     uint64_t *order;     /* out: commit key per transaction                */
     uint8_t *status;     /* out: 1 committed, 2 gave up, 3 not run         */
-    void *out;           /* out: int32 (RMW) or uint64 (cache) per tx      */
-    uint32_t txid_base;  /* RMW: txid = txid_base + index                   */
+    void *out;           /* out: int32 (RMW, W2) or uint64 (cache) per tx  */
+    uint32_t txid_base;  /* RMW, W2: txid = txid_base + index               */
     uint32_t word_base;  /* BANK: account a is word word_base + a           */
 } hetm_batch;
 

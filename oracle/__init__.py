@@ -5,6 +5,7 @@ what a round must produce, from the definitions in the paper
 (arXiv 1905.00661):
 
 * ``replay_*``   -- serial replay in the reported commit order (P1, Sec. III)
+                    of bank, W1, W2 (Sec. V-A) and object-cache batches,
                     plus the exact read/write granule sets (Sec. IV-B/IV-C);
 * ``conflicts``  -- CPU write-set vs GPU read-set by brute-force set
                     intersection (Sec. IV-C, Validation Phase);
@@ -72,6 +73,9 @@ def lib():
         L.hetm_oracle_replay_rmw.argtypes = [vp, u64, vp, u64, vp, vp, u32, vp, u32, u32, vp, u64, vp,
                                              vp, u64, vp]
         L.hetm_oracle_replay_rmw.restype = ci
+        L.hetm_oracle_replay_w2.argtypes = [vp, u64, vp, u64, vp, vp, u32, vp, u32, u32, vp, u64, vp,
+                                            vp, u64, vp]
+        L.hetm_oracle_replay_w2.restype = ci
         L.hetm_oracle_replay_cache.argtypes = [vp, u64, u32, u64, u64, u64, u64, vp, u64, vp, vp, vp,
                                                u32, u32, vp, u64, vp, vp, u64, vp]
         L.hetm_oracle_replay_cache.restype = ci
@@ -129,6 +133,20 @@ def replay_rmw(stmr, txs, order, status, granule_bytes, chunk_bytes, txid_base=0
                                       _p(nr), _p(d), d.size, _p(nd))
     if rc != 0:
         raise ValueError("oracle rmw replay failed")
+    return out, r[: int(nr[0])].copy(), d[: int(nd[0])].copy()
+
+
+def replay_w2(stmr, txs, order, status, granule_bytes, chunk_bytes, txid_base=0):
+    """Replay W2 transactions (40 reads, updates write their first 4 words);
+    returns (out_sum int32[n], R, D)."""
+    order, status = _u64(order), _u8(status)
+    out = np.zeros(len(txs), np.int32)
+    r, d, nr, nd = _sets_out(40 * len(txs), 4 * len(txs))
+    rc = lib().hetm_oracle_replay_w2(_p(stmr), stmr.size, _p(txs), len(txs), _p(order), _p(status),
+                                     txid_base, _p(out), granule_bytes, chunk_bytes, _p(r), r.size,
+                                     _p(nr), _p(d), d.size, _p(nd))
+    if rc != 0:
+        raise ValueError("oracle W2 replay failed")
     return out, r[: int(nr[0])].copy(), d[: int(nd[0])].copy()
 
 

@@ -52,6 +52,13 @@ struct RmwTx {
 };
 static_assert(sizeof(RmwTx) == 20, "rmw tx is 20 bytes");
 
+struct W2Tx {
+    uint32_t addr[40];
+    uint32_t flags;    // bit 0: update transaction
+    uint32_t pad[3];
+};
+static_assert(sizeof(W2Tx) == 176, "W2 tx is 176 bytes");
+
 struct CacheReq {
     uint64_t key;
     uint64_t value;
@@ -169,6 +176,44 @@ int hetm_oracle_replay_rmw(int32_t* stmr, uint64_t n_words, const void* txs, uin
         const RmwTx& t = tx[i];
         int32_t s = 0;
         for (int j = 0; j < 4; ++j) {
+            if (t.addr[j] >= n_words) return -1;
+            s = add32(s, stmr[t.addr[j]]);
+            fp.read(t.addr[j]);
+        }
+        out_sum[i] = s;
+        if (t.flags & 1u) {
+            uint32_t txid = txid_base + (uint32_t)i;
+            for (int j = 0; j < 4; ++j) {
+                stmr[t.addr[j]] = add32(add32(s, j), (int32_t)txid);
+                fp.write(t.addr[j]);
+            }
+        }
+    }
+    int64_t a = emit(fp.granules, r_out, r_cap), b = emit(fp.chunks, d_out, d_cap);
+    if (a < 0 || b < 0) return -1;
+    *n_r = (uint64_t)a;
+    *n_d = (uint64_t)b;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Serial replay of W2 transactions (Sec. V-A: W1 with 40 reads instead of 4
+// in both transaction types).  Each reads its 40 words and outputs their
+// 32-bit wrapping sum s; an update transaction then writes s + j + txid to
+// its first 4 words, j = 0..3 (both workloads' updates update 4 positions).
+// Outputs and footprints as for hetm_oracle_replay_rmw.
+// ---------------------------------------------------------------------------
+int hetm_oracle_replay_w2(int32_t* stmr, uint64_t n_words, const void* txs, uint64_t n_tx,
+                          const uint64_t* order, const uint8_t* status, uint32_t txid_base,
+                          int32_t* out_sum, uint32_t granule_bytes, uint32_t chunk_bytes,
+                          uint32_t* r_out, uint64_t r_cap, uint64_t* n_r,
+                          uint32_t* d_out, uint64_t d_cap, uint64_t* n_d) {
+    const W2Tx* tx = static_cast<const W2Tx*>(txs);
+    Footprint fp{{}, {}, granule_bytes, chunk_bytes};
+    for (uint64_t i : serial_order(n_tx, order, status)) {
+        const W2Tx& t = tx[i];
+        int32_t s = 0;
+        for (int j = 0; j < 40; ++j) {
             if (t.addr[j] >= n_words) return -1;
             s = add32(s, stmr[t.addr[j]]);
             fp.read(t.addr[j]);

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libhetm.so")
 
 HETM_OK, HETM_EINVAL, HETM_ENOMEM, HETM_ECAPACITY = 0, -1, -2, -3
 HETM_ETIMEOUT, HETM_ECUDA, HETM_EBUSY, HETM_EDEVICE = -4, -5, -6, -7
-HETM_WL_BANK, HETM_WL_RMW, HETM_WL_CACHE = 1, 2, 3
+HETM_WL_BANK, HETM_WL_RMW, HETM_WL_CACHE, HETM_WL_W2 = 1, 2, 3, 4
 HETM_POLICY_GPU_LOSES, HETM_POLICY_CPU_LOSES = 0, 1
 HETM_OUTCOME_CLEAN, HETM_OUTCOME_GPU_ROLLED_BACK, HETM_OUTCOME_CPU_DISCARDED = 0, 1, 2
 HETM_EXEC_ORDERED, HETM_EXEC_OPTIMISTIC = 0, 1
@@ -49,7 +49,7 @@ class hetm_config(ctypes.Structure):
                 ("cache_ver_base", _u64), ("exec_mode", _u32), ("early_validate", _u32),
                 ("max_round_tx", _u64), ("dev_alloc", _ALLOC), ("dev_free", _FREE),
                 ("alloc_user", _vp), ("conflict_policy", _u32), ("starve_limit", _u32),
-                ("exec_budget_us", _u32)]
+                ("exec_budget_us", _u32), ("uninstrumented", _u32)]
 
 
 class hetm_batch(ctypes.Structure):

@@ -357,6 +357,7 @@ ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
     a.val_base = c->cfg.cache_val_base;
     a.lru_base = c->cfg.cache_lru_base;
     a.ver_base = c->cfg.cache_ver_base;
+    a.instrument = c->cfg.uninstrumented ? 0u : 1u;
     return a;
 }
 
@@ -825,8 +826,10 @@ int hetm_sync(hetm_ctx *c) {
 
 int hetm_gpu_submit_batch(hetm_ctx *c, const hetm_batch *b, uint64_t *batch_id) {
     if (!c || !b) return HETM_EINVAL;
-    if (b->workload < HETM_WL_BANK || b->workload > HETM_WL_CACHE) return HETM_EINVAL;
+    if (b->workload < HETM_WL_BANK || b->workload > HETM_WL_W2) return HETM_EINVAL;
     if (b->n_tx && !b->tx) return HETM_EINVAL;
+    // W2 (40 reads) runs under the optimistic executor only
+    if (b->workload == HETM_WL_W2 && c->cfg.exec_mode != HETM_EXEC_OPTIMISTIC) return HETM_EINVAL;
     if (b->workload == HETM_WL_CACHE) {
         const hetm_config &f = c->cfg;
         const uint64_t ns = 1ull << f.cache_log2_sets;

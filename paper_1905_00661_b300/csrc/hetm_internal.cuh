@@ -94,6 +94,9 @@ struct ExecArgs {
     uint32_t *rest;
     unsigned long long *rest_n;
     uint64_t rest_cap;
+    // 0: commits record nothing in RS_bmp / WS_bmp (the uninstrumented
+    // executor that instrumentation costs are measured against, Sec. V-A)
+    uint32_t instrument;
 };
 
 // One transaction of the ordered phase (indexed by its rank in that phase).

@@ -35,12 +35,13 @@ size_t record_bytes(uint32_t wl) {
         case HETM_WL_BANK: return sizeof(hetm_bank_tx);
         case HETM_WL_RMW: return sizeof(hetm_rmw_tx);
         case HETM_WL_CACHE: return sizeof(hetm_cache_req);
+        case HETM_WL_W2: return sizeof(hetm_w2_tx);
         default: return 0;
     }
 }
 
 size_t out_bytes(uint32_t wl) {
-    return wl == HETM_WL_RMW ? 4 : wl == HETM_WL_CACHE ? 8 : 0;
+    return wl == HETM_WL_RMW || wl == HETM_WL_W2 ? 4 : wl == HETM_WL_CACHE ? 8 : 0;
 }
 
 struct Req {

@@ -21,7 +21,13 @@
 //     nothing changed, with commit key 2 * (newest version seen) + 1, i.e.
 //     right after the last writer it observed;
 //   * a cache GET that hits writes its LRU stamp: it locks that stripe at
-//     commit, takes v, then re-validates what it read (TL2 order).
+//     commit, takes v, then re-validates what it read (TL2 order);
+//   * a W2 transaction (40 reads, Sec. V-A) reads against a snapshot rv of
+//     the clock: it locks its 4 written words first (updates), checks that
+//     every other word's stripe is unlocked with a version <= rv, fences,
+//     reads the values, and after taking v checks the stripes again (TL2:
+//     any writer that could have come between rv and v shows there).  An
+//     update commits at 2v, a read-only transaction at 2 rv + 1.
 //
 // At commit a transaction ORs the granules of every word it read or wrote
 // into RS_bmp and the chunks of every word it wrote into WS_bmp (Sec. IV-B,
@@ -43,10 +49,12 @@ struct Exec {
     }
     __device__ __forceinline__ unsigned long long *lock(uint32_t s) const { return a.locks + s; }
     __device__ __forceinline__ void mark_read(uint64_t w0, uint32_t len) const {
+        if (!a.instrument) return;
         for (uint64_t g = w0 >> a.gshift; g <= (w0 + len - 1) >> a.gshift; ++g)
             rs_mark(a.rs, a.filter, g);
     }
     __device__ __forceinline__ void mark_write(uint64_t w0, uint32_t len) const {
+        if (!a.instrument) return;
         mark_read(w0, len);
         for (uint64_t c = w0 >> a.cshift; c <= (w0 + len - 1) >> a.cshift; ++c)
             atomicOr(a.ws + (c >> 5), 1u << (c & 31));
@@ -110,6 +118,31 @@ __device__ __forceinline__ void release(const Exec &x, const uint32_t (&st)[N], 
         if (own & (1u << k)) st_rlx64(x.lock(st[k]), word);
 }
 
+// W2: a word's stripe is usable when this lane holds it or when it is
+// unlocked at a version no newer than the snapshot rv.
+__device__ __forceinline__ bool w2_stripe_ok(const Exec &x, uint64_t w, unsigned long long rv,
+                                             unsigned long long mine) {
+    const unsigned long long l = ld_rlx64(x.lock(x.stripe(w)));
+    return l == mine || (!(l & 1ull) && (l >> 1) <= rv);
+}
+
+// Stripes of words j0..39 of a W2 transaction (all usable: true).
+__device__ __forceinline__ bool w2_check(const Exec &x, const hetm_w2_tx *t, int j0,
+                                         unsigned long long rv, unsigned long long mine) {
+    bool ok = true;
+#pragma unroll 4
+    for (int j = j0; j < 40; ++j) ok &= w2_stripe_ok(x, __ldg(&t->addr[j]), rv, mine);
+    return ok;
+}
+
+// 32-bit wrapping sum of words j0..39 (after w2_check and a fence).
+__device__ __forceinline__ int32_t w2_sum(const Exec &x, const hetm_w2_tx *t, int j0) {
+    int32_t s = 0;
+#pragma unroll 4
+    for (int j = j0; j < 40; ++j) s += ld_rlx32(x.a.W + __ldg(&t->addr[j]));
+    return s;
+}
+
 __device__ __forceinline__ int binsearch(const uint64_t *prefix, uint32_t n, uint64_t gi) {
     uint32_t lo = 0, hi = n;  // prefix[lo] <= gi < prefix[hi]
     while (hi - lo > 1) {
@@ -140,6 +173,7 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
     int32_t amt = 0;
     uint64_t ckey = 0, cval = 0;
     uint32_t cop = 0;
+    const hetm_w2_tx *w2 = nullptr;  // W2: the record (its 40 words are re-read from it)
     uint64_t *o_order = nullptr;
     uint8_t *o_status = nullptr;
     void *o_out = nullptr;
@@ -207,6 +241,16 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
                         cval = r->value;
                         cop = r->op;
                         na = 0;
+                    } else if (wl == HETM_WL_W2) {
+                        w2 = static_cast<const hetm_w2_tx *>(d.tx) + li;
+                        for (int k = 0; k < 40; ++k) {
+                            const uint32_t ad = w2->addr[k];
+                            if (k < 4) addr[k] = ad;
+                            bad |= ad >= a.n_words;
+                        }
+                        upd = w2->flags & 1u;
+                        txid = d.txid_base + li;
+                        na = 4;
                     } else {
                         bad = true;
                     }
@@ -215,7 +259,7 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
                         if (o_status) o_status[li] = kGaveUp;
                         ++n_gaveup;
                         gi = kNone;  // drawn again next iteration
-                    } else if (a.skip_ro && wl == HETM_WL_RMW && !upd) {
+                    } else if (a.skip_ro && (wl == HETM_WL_RMW || wl == HETM_WL_W2) && !upd) {
                         gi = kNone;  // ran in the read-only phase
                     } else if (expired) {
                         if (o_status) o_status[li] = kGaveUp;
@@ -252,7 +296,39 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
         bool evict = false;
         int32_t ver_old = 0;
 
-        if (active && wl != HETM_WL_CACHE) {
+        unsigned long long rv = 0;  // W2: clock snapshot
+        if (active && wl == HETM_WL_W2) {
+            rv = ld_rlx64(a.gv);
+            fence_gpu();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) st[k] = x.stripe(addr[k]);
+            bool ok = true, locked = false;
+            if (upd) ok = locked = try_lock<4>(x, st, 4, cur, own, mine);
+            // updates hold their 4 words; the rest (all 40 for a read-only
+            // transaction) must be unlocked at a version <= rv
+            if (ok) ok = w2_check(x, w2, upd ? 4 : 0, rv, mine);
+            if (ok) {
+                fence_gpu();
+                if (upd) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) val[k] = ld_rlx32(a.W + addr[k]);
+                    val[0] += w2_sum(x, w2, 4);  // val[0..3] summed at commit
+                    want_v = true;
+                } else {
+                    val[0] = w2_sum(x, w2, 0);
+                    fence_gpu();
+                    ro_ok = w2_check(x, w2, 0, rv, mine);
+                    fail = !ro_ok;
+                    ro_key = 2 * rv + 1;
+                }
+            } else {
+                // nothing written: give the stripes back at their versions
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (locked && (own & (1u << k))) st_rlx64(x.lock(st[k]), cur[k]);
+                fail = true;
+            }
+        } else if (active && wl != HETM_WL_CACHE) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) st[k] = x.stripe(addr[k]);
             if (upd) {
@@ -386,7 +462,33 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
 
         // ------------------------------- phase 2: validate, write, release
         bool committed = false;
-        if (want_v && wl != HETM_WL_CACHE) {
+        if (want_v && wl == HETM_WL_W2) {
+            // TL2 commit: a writer of a read word that came after rv shows
+            // in its stripe now (locked, or a version > rv)
+            fence_gpu();
+            if (w2_check(x, w2, 4, rv, mine)) {
+                const int32_t s = val[0] + val[1] + val[2] + val[3];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) st_rlx32(a.W + addr[k], s + k + (int32_t)txid);
+                release<4>(x, st, own, v << 1);
+                if (o_order) o_order[li] = v << 1;
+                if (o_out) static_cast<int32_t *>(o_out)[li] = s;
+                for (int j = 4; j < 40; ++j) x.mark_read(__ldg(&w2->addr[j]), 1);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) x.mark_write(addr[k], 1);
+                committed = true;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (own & (1u << k)) st_rlx64(x.lock(st[k]), cur[k]);
+                fail = true;
+            }
+        } else if (ro_ok && wl == HETM_WL_W2) {
+            if (o_order) o_order[li] = ro_key;
+            if (o_out) static_cast<int32_t *>(o_out)[li] = val[0];
+            for (int j = 0; j < 40; ++j) x.mark_read(__ldg(&w2->addr[j]), 1);
+            committed = true;
+        } else if (want_v && wl != HETM_WL_CACHE) {
             int32_t nv[4];
             int32_t s = 0;
             if (wl == HETM_WL_RMW) {
@@ -408,7 +510,7 @@ __global__ void __launch_bounds__(256) k_exec(ExecArgs a) {
             for (int k = 0; k < 4; ++k)
                 if (k < (int)na) x.mark_write(addr[k], 1);
             committed = true;
-        } else if (ro_ok && wl != HETM_WL_CACHE) {
+        } else if (ro_ok && wl != HETM_WL_CACHE && wl != HETM_WL_W2) {
             int32_t s = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) s += val[k];

@@ -501,8 +501,29 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
     auto run_ro = [&](uint64_t u) -> bool {
         const int b = find_batch(a.prefix, a.rp->n_batches, u);
         const DevBatch &d = a.batches[b];
-        if (d.workload != HETM_WL_RMW) return false;
         const uint32_t li = (uint32_t)(u - a.prefix[b]);
+        if (d.workload == HETM_WL_W2) {  // W2 read-only: 40 words
+            const hetm_w2_tx *x = static_cast<const hetm_w2_tx *>(d.tx) + li;
+            if (x->flags & 1u) return false;
+            bool ok = true;
+            int32_t s = 0;
+#pragma unroll 8
+            for (int k = 0; k < 40; ++k) {
+                const uint32_t ad = __ldg(&x->addr[k]);
+                ok &= ad < a.n_words;
+                if (ad < a.n_words) s += a.W[ad];
+            }
+            if (!ok) return false;  // reported by the STM
+            if (a.instrument) {
+#pragma unroll 8
+                for (int k = 0; k < 40; ++k) rs_mark(a.rs, a.filter, __ldg(&x->addr[k]) >> a.gshift);
+            }
+            if (d.order) d.order[li] = key;
+            if (d.out) static_cast<int32_t *>(d.out)[li] = s;
+            if (d.status) d.status[li] = kCommitted;
+            return true;
+        }
+        if (d.workload != HETM_WL_RMW) return false;
         const hetm_rmw_tx *x = static_cast<const hetm_rmw_tx *>(d.tx) + li;
         if (x->flags & 1u) return false;
         uint32_t ad[4];
@@ -516,8 +537,10 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
         int32_t s = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) s += a.W[ad[k]];
+        if (a.instrument) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) rs_mark(a.rs, a.filter, ad[k] >> a.gshift);
+            for (int k = 0; k < 4; ++k) rs_mark(a.rs, a.filter, ad[k] >> a.gshift);
+        }
         if (d.order) d.order[li] = key;
         if (d.out) static_cast<int32_t *>(d.out)[li] = s;
         if (d.status) d.status[li] = kCommitted;
@@ -573,6 +596,7 @@ __global__ void __launch_bounds__(256) k_ord_ro(OrderArgs o) {
 }
 
 __device__ __forceinline__ void mark_range(const ExecArgs &a, uint64_t w0, uint32_t len, bool write) {
+    if (!a.instrument) return;
     for (uint64_t g = w0 >> a.gshift; g <= (w0 + len - 1) >> a.gshift; ++g)
         rs_mark(a.rs, a.filter, g);
     if (write)

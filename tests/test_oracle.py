@@ -137,6 +137,55 @@ def test_golden_cache_sets():
     assert R.tolist() == ex["R"] and D.tolist() == ex["D"]
 
 
+def _w2_golden_txs(g):
+    txs = np.zeros(len(g["txs"]), wl.W2_DTYPE)
+    spans = [list(range(0, 40)), list(range(2, 42)), [47, 46, 45, 44] + list(range(0, 36))]
+    for i, t in enumerate(g["txs"]):
+        txs[i]["addr"] = spans[i]
+        txs[i]["flags"] = t["flags"]
+    return txs
+
+
+def test_golden_w2():
+    """Sec. V-A W2 (40 reads): hand-derived sums and final words for two serial
+    orders of the same three transactions."""
+    g = _golden("w2_order.json")
+    txs = _w2_golden_txs(g)
+    for case in g["cases"]:
+        st = np.arange(g["n_words"], dtype=np.int32)
+        out, R, D = oracle.replay_w2(st, txs, case["order"], np.ones(3, np.uint8),
+                                     g["granule_bytes"], g["chunk_bytes"])
+        assert out.tolist() == case["out"]
+        assert st[0:4].tolist() == g["expect_common"]["final_0_3"]
+        assert st[44:48].tolist() == case["final_44_47"]
+        assert st[4:44].tolist() == list(range(4, 44))
+        assert R.tolist() == g["expect_common"]["R"] and D.tolist() == g["expect_common"]["D"]
+
+
+def test_w2_with_zero_padding_reads_is_w1():
+    """A W2 transaction whose 36 extra words hold 0 and are never written
+    computes what the W1 transaction on its first 4 words computes."""
+    n = 1 << 12
+    w1 = wl.rmw_batch(seed=5, batch=0, n_tx=300, log2_words=11, update_frac=0.5)
+    w2 = np.zeros(len(w1), wl.W2_DTYPE)
+    w2["addr"][:, :4] = w1["addr"]
+    w2["addr"][:, 4:] = (n // 2 + np.arange(36, dtype=np.uint32))[None, :] + \
+        (np.arange(len(w1), dtype=np.uint32) % 7)[:, None] * 36
+    w2["flags"] = w1["flags"]
+    start = wl.init_words(5, 0, n)
+    start[n // 2:] = 0
+    order = np.arange(len(w1), dtype=np.uint64)[::-1] * 2 + 2   # reverse launch order
+    status = np.ones(len(w1), np.uint8)
+    s1, s2 = start.copy(), start.copy()
+    o1, R1, D1 = oracle.replay_rmw(s1, w1, order, status, 4, 64, txid_base=11)
+    o2, R2, D2 = oracle.replay_w2(s2, w2, order, status, 4, 64, txid_base=11)
+    np.testing.assert_array_equal(o1, o2)
+    np.testing.assert_array_equal(s1, s2)
+    np.testing.assert_array_equal(D1, D2)
+    np.testing.assert_array_equal(R2[R2 < n // 2], R1)
+    assert (R2 >= n // 2).sum() == 36 + 6 * 36   # the padding words, one granule each
+
+
 def test_cache_replay_finds_every_prefilled_key():
     """The prefill places keys by workloads.mix64 (pinned to published
     SplitMix64 outputs); a GET of every placed key through the oracle's own

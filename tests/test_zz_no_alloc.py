@@ -65,8 +65,8 @@ def test_noalloc_matches_validate_only_on_two_calls(hetm):
             o_flags, o_n = oracle.conflicts(v.log[:n], v.read_granules, v.granule_bytes)
             np.testing.assert_array_equal(got, o_flags)
             assert int(cnt.item()) == o_n
-        # the planted recipe fixes the hit count of the full log
-        assert int(ref_cnt.item()) == v.n_hits_planted
+            if n == len(v.log):  # the planted recipe fixes the hit count of the full log
+                assert o_n == v.n_hits_planted
 
 
 @pytest.mark.gpu

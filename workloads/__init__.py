@@ -36,6 +36,7 @@ BANK_DTYPE = np.dtype([("src", "<u4"), ("dst", "<u4"), ("amount", "<i4")])
 #: W1-style transaction: 4 word addresses, flags bit0 = update (Sec. V-A)
 RMW_DTYPE = np.dtype([("addr", "<u4", (4,)), ("flags", "<u4")])
 #: object-cache request (Sec. V-D): op 0 = GET, 1 = PUT
+W2_DTYPE = np.dtype([("addr", "<u4", (40,)), ("flags", "<u4"), ("pad", "<u4", (3,))])
 CACHE_DTYPE = np.dtype([("key", "<u8"), ("value", "<u8"), ("op", "<u4"), ("pad", "<u4")])
 
 assert LOG_DTYPE.itemsize == 12 and BANK_DTYPE.itemsize == 12
@@ -44,6 +45,7 @@ assert RMW_DTYPE.itemsize == 20 and CACHE_DTYPE.itemsize == 24
 WORKLOAD_BANK = 1
 WORKLOAD_RMW = 2
 WORKLOAD_CACHE = 3
+WORKLOAD_W2 = 4
 
 # --------------------------------------------------------------------------
 # counter-based SplitMix64
@@ -176,6 +178,7 @@ class S:
     GRAN, HIT_G, HIT_W, ZIPF, VAL, TS, POS = 10, 11, 12, 13, 14, 15, 16
     PLANT, PLANT_VAL = 17, 18
     RMW_ADDR, RMW_UPD = 20, 21
+    W2_ADDR, W2_UPD = 24, 25
     LOG_ADDR, LOG_VAL = 22, 23
     KEY, OP, PUTVAL, PREFILL = 30, 31, 32, 33
     ARRIVE, SIZE, KIND = 40, 41, 42
@@ -416,6 +419,37 @@ def rmw_batch(seed: int, batch: int, n_tx: int, log2_words: int, q: float = 0.99
             raise RuntimeError("duplicate redraw did not converge")
     tx["addr"] = addr
     upd = uniform01(draws_range(seed, S.RMW_UPD, n_tx, batch * n_tx)) < update_frac
+    tx["flags"] = upd.astype(np.uint32)
+    return tx
+
+
+def w2_batch(seed: int, batch: int, n_tx: int, log2_words: int, update_frac: float = 0.10,
+             lo: int = 0, hi: int | None = None) -> np.ndarray:
+    """W2 of Sec. V-A: transactions of 40 distinct words drawn uniformly over
+    [lo, hi); ``update_frac`` of them are updates (they write their first 4
+    words).  A transaction with a repeated word is redrawn whole."""
+    hi = (1 << log2_words) if hi is None else hi
+    tx = np.zeros(n_tx, dtype=W2_DTYPE)
+    base = batch * n_tx * 40
+
+    def gen(c0, rows):
+        ctr = np.arange(c0, c0 + rows * 40, dtype=np.uint64)
+        return (uniform_below(draws(seed, S.W2_ADDR, ctr), hi - lo)
+                + np.uint64(lo)).astype(np.uint32).reshape(rows, 40)
+
+    addr = gen(base, n_tx)
+    extra = 0
+    while True:
+        srt = np.sort(addr, axis=1)
+        rows = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
+        if rows.size == 0:
+            break
+        extra += 1
+        addr[rows] = gen((1 << 41) + (batch << 24) * 64 + extra * (n_tx * 40), rows.size)
+        if extra > 256:
+            raise RuntimeError("duplicate redraw did not converge")
+    tx["addr"] = addr
+    upd = uniform01(draws_range(seed, S.W2_UPD, n_tx, batch * n_tx)) < update_frac
     tx["flags"] = upd.astype(np.uint32)
     return tx
 
