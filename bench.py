@@ -312,10 +312,11 @@ def bench_ours(args, rank, world, local_rank, inputs):
 
 def bench_validation(torch, h, v, reps=20):
     """Kernel V alone on the 16M-tuple log (12 B/tuple + 1 flag bit), 2^28 words, G = 64 B."""
+    import paper_1905_00661_b300.testing as hetm_testing
     n = len(v.log)
     with h.Context(1 << LOG2W, v.granule_bytes, {"log_capacity": 1 << 12}) as vc:
         first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
-        vc.gpu_mark(torch.from_numpy(first).cuda())
+        hetm_testing.gpu_mark(vc, torch.from_numpy(first).cuda())
         dlog = torch.from_numpy(v.log.view(np.uint8)).cuda()
         flags = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -354,6 +355,7 @@ def bench_round_at_scale(torch, h, v, reps=5):
     G = 64 B, 16 KB chunks): planted read set and GPU writes, 16M-entry CPU log.
     Two variants: the log as generated (2% hits: conflict, dirty chunks S -> W)
     and the log without its hits (clean: dirty chunks W -> S)."""
+    import paper_1905_00661_b300.testing as hetm_testing
     wpg = v.granule_bytes // 4
     first = torch.from_numpy((v.read_granules.astype(np.uint64) * wpg).astype(np.uint32)).cuda()
     paddr = torch.from_numpy(v.plant_addr).cuda()
@@ -369,12 +371,12 @@ def bench_round_at_scale(torch, h, v, reps=5):
             rows = []
             t_end = time.perf_counter() + 0.3  # busy before timing (see bench_validation)
             while time.perf_counter() < t_end:
-                c.gpu_mark(first)
+                hetm_testing.gpu_mark(c, first)
                 c.log_attach(dlog, n)
                 c.round(stats=True)
             for r in range(reps + 1):
-                c.gpu_mark(first)
-                c.gpu_mark(paddr, pval)
+                hetm_testing.gpu_mark(c, first)
+                hetm_testing.gpu_mark(c, paddr, pval)
                 c.log_attach(dlog, n)
                 st = c.round(stats=True)
                 if r:
@@ -694,6 +696,7 @@ def config_dict(world, tuned=None):
 
 def run_case(name):
     """Small single-shot cases used for ncu captures (a few GB on the device)."""
+    import paper_1905_00661_b300.testing as hetm_testing
     import torch
 
     import paper_1905_00661_b300 as h
@@ -734,7 +737,7 @@ def run_case(name):
         v = wl.validation_round(seed=1, log2_words=27, granule_bytes=32, with_init=False)
         with h.Context(1 << 27, 32, {"log_capacity": 1 << 12, "exec_mode": 1}) as ctx:
             first = (v.read_granules.astype(np.uint64) * 8).astype(np.uint32)
-            ctx.gpu_mark(torch.from_numpy(first).cuda())
+            hetm_testing.gpu_mark(ctx, torch.from_numpy(first).cuda())
             dlog = torch.from_numpy(v.log.view(np.uint8)).cuda()
             flags = torch.zeros((len(v.log) + 31) // 32, dtype=torch.int32, device="cuda")
             cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -770,8 +773,8 @@ def run_case(name):
         with h.Context(1 << 27, 64, {"log_capacity": 1 << 12, "cpu_threads": 1}) as ctx:
             ctx.load(torch.zeros(1 << 27, dtype=torch.int32, device="cuda"))
             first = torch.from_numpy((v.read_granules.astype(np.uint64) * wpg).astype(np.uint32)).cuda()
-            ctx.gpu_mark(first)
-            ctx.gpu_mark(torch.from_numpy(v.plant_addr).cuda(), torch.from_numpy(v.plant_value).cuda())
+            hetm_testing.gpu_mark(ctx, first)
+            hetm_testing.gpu_mark(ctx, torch.from_numpy(v.plant_addr).cuda(), torch.from_numpy(v.plant_value).cuda())
             dlog = torch.from_numpy(v.log.view(np.uint8)).cuda()
             ctx.log_attach(dlog, len(v.log))
             st = ctx.round(stats=True)
@@ -883,9 +886,10 @@ def main():
     if rank != 0:
         return
     import paper_1905_00661_b300 as h
+    import paper_1905_00661_b300.testing as hetm_testing
     chain = [critical_path(b) for b in inputs[1]]
-    handoff_g, handoff_s = h.handoff_latency(20000)
-    ra = h.random_access_rate(LOG2W, 1 << 28)
+    handoff_g, handoff_s = hetm_testing.handoff_latency(20000)
+    ra = hetm_testing.random_access_rate(LOG2W, 1 << 28)
     contention = bench_contention(torch, h, inputs, res["tuned"])
     host_merge = bench_host_merge(torch, h, inputs, res["tuned"])
     w1 = [bench_w1_uniform(torch, h, inputs[0], f) for f in (0.1, 1.0)]

@@ -277,10 +277,6 @@ HETM_API int hetm_gpu_exec(hetm_ctx *ctx, int per_batch);
  * transactions that gave up, and aborted attempts.  Synchronizes. */
 HETM_API int hetm_exec_counters(hetm_ctx *ctx, uint64_t *committed, uint64_t *gave_up, uint64_t *aborts);
 
-/* Non-transactional instrumentation of words the GPU read (vals NULL) or
- * wrote (STMR^W[addr[i]] = vals[i]) -- a planted GPU batch.  Device
- * pointers, asynchronous. */
-HETM_API int hetm_gpu_mark(hetm_ctx *ctx, const uint32_t *addr, const int32_t *vals, uint64_t n);
 
 /* ---------------------------------------------------- log shipping (A2) */
 /* Append n tuples (host memory) to CPU thread `thread`'s pinned log.  Each
@@ -607,31 +603,6 @@ HETM_API int hetm_dispatch_wait(hetm_dispatch *d, uint64_t ticket, double *laten
 HETM_API int hetm_dispatch_get_stats(hetm_dispatch *d, hetm_dispatch_stats *out);
 /* Run every queued request, stop the threads, free the dispatcher. */
 HETM_API void hetm_dispatch_destroy(hetm_dispatch *d);
-
-/* ---------------------------------------------------- handoff latency */
-/* Committing in a fixed order serializes the writers of every word, so a
- * batch cannot execute faster than its longest chain of conflicting
- * transactions times the time one transaction needs to hand a word on to
- * the next (the serialization-depth bound).  This measures that hand-on on
- * the current device with nothing else running: *global_ns, a token
- * bounced between two CTAs on two SMs through one global word (acquire
- * load / release store, cooperative launch); *shared_ns, between two warps
- * of one CTA through shared memory.  Each is the mean over 2 x rounds
- * one-way hand-ons.  Either pointer may be NULL.  Synchronous; allocates 40
- * bytes of device memory for the call.  Every wait is bounded (1 s):
- * HETM_ETIMEOUT if one gave up. */
-HETM_API int hetm_handoff_latency(uint32_t rounds, double *global_ns, double *shared_ns);
-
-/* Random-sector rate of the current device: n_access random 4-byte reads
- * (*read_per_s) and writes (*write_per_s) spread over a 2^log2_words-word
- * array (20 <= log2_words <= 32; choose it larger than L2 so that every
- * access is a DRAM sector), eight in flight per thread, timed with CUDA
- * events after one warm-up pass.  This is the roofline of scattered work:
- * the executor's word accesses and the apply's timestamp probes and winner
- * writes.  Allocates and frees the array; synchronous.  Either pointer may
- * be NULL, not both. */
-HETM_API int hetm_random_access_rate(uint32_t log2_words, uint64_t n_access, double *read_per_s,
-                                     double *write_per_s);
 
 /* ------------------------------------------------------------ autotuner */
 /* The paper runs one executor shape and studies the conflict granule (Sec.

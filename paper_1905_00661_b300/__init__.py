@@ -80,13 +80,13 @@ class hetm_round_stats(ctypes.Structure):
 #: every symbol include/hetm.h declares
 SYMBOLS = ("hetm_strerror", "hetm_config_default", "hetm_init", "hetm_destroy", "hetm_load",
            "hetm_read_stmr", "hetm_device_ptr", "hetm_bitmap_words", "hetm_sync",
-           "hetm_gpu_submit_batch", "hetm_gpu_exec", "hetm_exec_counters", "hetm_gpu_mark",
+           "hetm_gpu_submit_batch", "hetm_gpu_exec", "hetm_exec_counters",
            "hetm_cpu_log_write", "hetm_log_attach", "hetm_validate", "hetm_validate_only",
            "hetm_merge", "hetm_round", "hetm_validate_noalloc", "hetm_ctx_stream",
            "hetm_round_wait", "hetm_server_config_default", "hetm_server_create",
            "hetm_server_submit", "hetm_server_wait", "hetm_server_get_stats",
            "hetm_server_destroy", "hetm_tune_space_default", "hetm_autotune",
-           "hetm_handoff_latency", "hetm_random_access_rate", "hetm_read_dirty",
+           "hetm_read_dirty",
            "hetm_cpu_updates_allowed", "hetm_batch_poll", "hetm_server_wait_outcome",
            "hetm_dispatch_config_default", "hetm_dispatch_create", "hetm_dispatch_register",
            "hetm_dispatch_submit", "hetm_dispatch_wait", "hetm_dispatch_get_stats",
@@ -175,7 +175,6 @@ def _declare(L):
         "hetm_gpu_submit_batch": (_int, [_vp, P(hetm_batch), P(_u64)]),
         "hetm_gpu_exec": (_int, [_vp, _int]),
         "hetm_exec_counters": (_int, [_vp, P(_u64), P(_u64), P(_u64)]),
-        "hetm_gpu_mark": (_int, [_vp, _vp, _vp, _u64]),
         "hetm_cpu_log_write": (_int, [_vp, _u32, _vp, _u32]),
         "hetm_log_attach": (_int, [_vp, _vp, _u64]),
         "hetm_validate": (_int, [_vp, P(_u64), _vp]),
@@ -201,8 +200,6 @@ def _declare(L):
         "hetm_server_get_stats": (_int, [_vp, P(hetm_server_stats)]),
         "hetm_server_destroy": (None, [_vp]),
         "hetm_tune_space_default": (_int, [P(hetm_tune_space)]),
-        "hetm_handoff_latency": (_int, [_u32, P(ctypes.c_double), P(ctypes.c_double)]),
-        "hetm_random_access_rate": (_int, [_u32, _u64, P(ctypes.c_double), P(ctypes.c_double)]),
         "hetm_read_dirty": (_int, [_vp, _vp, P(_u64), P(_u64)]),
         "hetm_read_dirty_async": (_int, [_vp, _vp, P(_u64), P(_u64)]),
         "hetm_read_dirty_wait": (_int, [_vp]),
@@ -294,20 +291,6 @@ def hetm_tune_space_default() -> hetm_tune_space:
     return sp
 
 
-def handoff_latency(rounds=20000):
-    """(cross-SM ns, cross-warp ns) for one hand-on of a word (hetm_handoff_latency)."""
-    g, sh = ctypes.c_double(), ctypes.c_double()
-    _ck(_lib.hetm_handoff_latency(int(rounds), ctypes.byref(g), ctypes.byref(sh)),
-        "hetm_handoff_latency")
-    return g.value, sh.value
-
-
-def random_access_rate(log2_words=28, n_access=1 << 28):
-    """(random 4-byte reads/s, writes/s) over a 2^log2_words-word array (hetm_random_access_rate)."""
-    r, w = ctypes.c_double(), ctypes.c_double()
-    _ck(_lib.hetm_random_access_rate(int(log2_words), int(n_access), ctypes.byref(r), ctypes.byref(w)),
-        "hetm_random_access_rate")
-    return r.value, w.value
 
 
 _TUNED = ("exec_mode", "exec_threads", "exec_blocks", "lock_log2", "ws_chunk_bytes")
@@ -470,11 +453,6 @@ class Context:
         c, g, a = _u64(), _u64(), _u64()
         rc = _lib.hetm_exec_counters(self.h, ctypes.byref(c), ctypes.byref(g), ctypes.byref(a))
         return {"committed": c.value, "gave_up": g.value, "aborts": a.value, "rc": rc}
-
-    def gpu_mark(self, addr, vals=None):
-        self._enter()
-        _ck(_lib.hetm_gpu_mark(self.h, _ptr(addr), _ptr(vals), len(addr)), "hetm_gpu_mark")
-        self._leave()
 
     # ------------------------------------------------------------- CPU logs
     def cpu_log_write(self, thread, entries: np.ndarray):

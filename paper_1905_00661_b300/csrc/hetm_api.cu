@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "hetm_internal.cuh"
+#include "hetm_testing.h"  // hetm_gpu_mark
 
 using namespace hetm;
 

@@ -1,4 +1,5 @@
-"""The C-ABI library loads and exports every symbol include/hetm.h declares (no GPU)."""
+"""The C-ABI libraries load and export every symbol include/hetm.h and
+include/hetm_testing.h declare (no GPU)."""
 import ctypes
 import os
 import re
@@ -8,21 +9,31 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "hetm.h")).read()
+def _declared(header="hetm.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     return set(re.findall(r"HETM_API[^;(]*?\b(hetm_\w+)\s*\(", src))
 
 
 def test_header_declares_binding_symbols():
     import paper_1905_00661_b300 as h
+    import paper_1905_00661_b300.testing as t
     assert _declared() == set(h.SYMBOLS)
+    assert _declared("hetm_testing.h") == set(t.SYMBOLS)
+    assert not _declared() & _declared("hetm_testing.h")
 
 
 def test_library_exports_every_declared_symbol():
     import paper_1905_00661_b300 as h
+    import paper_1905_00661_b300.testing as t
     L = ctypes.CDLL(h.LIB_PATH)
     for name in _declared():
         assert hasattr(L, name), name
+    libs = {"libhetm.so": L, "libhetm_testing.so": ctypes.CDLL(t.LIB_PATH)}
+    for name, where in t.SYMBOLS.items():
+        assert hasattr(libs[where], name), name
+    # the probes are not part of the round library
+    for name in ("hetm_handoff_latency", "hetm_random_access_rate", "hetm_l2_probe_rate"):
+        assert not hasattr(L, name), name
 
 
 def test_strerror_and_defaults_without_gpu():
@@ -72,17 +83,21 @@ def test_autotune_space_and_argument_checks_without_gpu():
 
 def test_handoff_probe_rejects_bad_arguments_without_gpu():
     import paper_1905_00661_b300 as h
+    import paper_1905_00661_b300.testing as t
     g = ctypes.c_double()
-    assert h.lib().hetm_handoff_latency(0, ctypes.byref(g), None) == h.HETM_EINVAL
-    assert h.lib().hetm_handoff_latency(100, None, None) == h.HETM_EINVAL
+    assert t.lib().hetm_handoff_latency(0, ctypes.byref(g), None) == h.HETM_EINVAL
+    assert t.lib().hetm_handoff_latency(100, None, None) == h.HETM_EINVAL
 
 
 def test_random_access_probe_rejects_bad_arguments_without_gpu():
     import paper_1905_00661_b300 as h
+    import paper_1905_00661_b300.testing as t
     r = ctypes.c_double()
-    assert h.lib().hetm_random_access_rate(10, 100, ctypes.byref(r), None) == h.HETM_EINVAL
-    assert h.lib().hetm_random_access_rate(24, 0, ctypes.byref(r), None) == h.HETM_EINVAL
-    assert h.lib().hetm_random_access_rate(24, 100, None, None) == h.HETM_EINVAL
+    assert t.lib().hetm_l2_probe_rate(9, 100, 0, ctypes.byref(r)) == h.HETM_EINVAL
+    assert t.lib().hetm_l2_probe_rate(19, 100, 300 * 1024, ctypes.byref(r)) == h.HETM_EINVAL
+    assert t.lib().hetm_random_access_rate(10, 100, ctypes.byref(r), None) == h.HETM_EINVAL
+    assert t.lib().hetm_random_access_rate(24, 0, ctypes.byref(r), None) == h.HETM_EINVAL
+    assert t.lib().hetm_random_access_rate(24, 100, None, None) == h.HETM_EINVAL
 
 
 def test_early_validation_fields_keep_layouts():

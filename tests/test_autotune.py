@@ -83,7 +83,8 @@ def test_autotune_picks_best_and_avoids_false_conflicts(hetm):
 def test_handoff_latency_probe(hetm):
     """Hand-on of a word: through shared memory (two warps of a CTA) well under
     a microsecond, and no slower than across two SMs through L2."""
-    g, sh = hetm.handoff_latency(5000)
+    import paper_1905_00661_b300.testing as t
+    g, sh = t.handoff_latency(5000)
     assert 5.0 < sh < 2000.0
     assert 20.0 < g < 20000.0
     assert sh < g
@@ -91,5 +92,15 @@ def test_handoff_latency_probe(hetm):
 
 def test_random_access_probe(hetm):
     """Random 4-byte reads and writes over 1 GiB: between 1e9 and 1e12 per second."""
-    r, w = hetm.random_access_rate(28, 1 << 26)
+    import paper_1905_00661_b300.testing as t
+    r, w = t.random_access_rate(28, 1 << 26)
     assert 1e9 < r < 1e12 and 1e9 < w < 1e12
+
+
+def test_l2_probe(hetm):
+    """Random 4-byte probes of a 2 MiB (L2-resident) array in the validation
+    kernel's launch shape: faster than random DRAM sectors, below 1e13/s."""
+    import paper_1905_00661_b300.testing as t
+    p = t.l2_probe_rate(19, 1 << 24)
+    r, _ = t.random_access_rate(28, 1 << 26)
+    assert r < p < 1e13

@@ -17,6 +17,7 @@ import pytest
 
 import oracle
 import workloads as wl
+import paper_1905_00661_b300.testing as hetm_testing
 from roundkit import flags_of, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -47,7 +48,7 @@ def test_validate_only_full_size_every_flag(hetm, torch, vr):
     ref_flags, ref_n = oracle.conflicts(vr.log, vr.read_granules, vr.granule_bytes)
     assert ref_n == vr.n_hits_planted
     with h.Context(1 << LOG2W, vr.granule_bytes, {"log_capacity": 1 << 12}) as ctx:
-        ctx.gpu_mark(torch.from_numpy(_first_words(vr)).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(_first_words(vr)).cuda())
         dlog = to_dev(torch, vr.log)
         flags = torch.zeros((n + 31) // 32, dtype=torch.int32, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -82,8 +83,8 @@ def test_round_full_size_final_state(hetm, torch, vr, variant):
     assert bool(ref.conflict) == (variant == "conflict")
     with h.Context(1 << LOG2W, vr.granule_bytes, {"log_capacity": 1 << 12, "cpu_threads": 1}) as ctx:
         ctx.load(torch.zeros(1 << LOG2W, dtype=torch.int32, device="cuda"))
-        ctx.gpu_mark(torch.from_numpy(_first_words(vr)).cuda())
-        ctx.gpu_mark(torch.from_numpy(vr.plant_addr).cuda(), torch.from_numpy(vr.plant_value).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(_first_words(vr)).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(vr.plant_addr).cuda(), torch.from_numpy(vr.plant_value).cuda())
         dlog = to_dev(torch, log)
         ctx.log_attach(dlog, len(log))
         st = ctx.round(stats=True)

@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 import workloads as wl
+import paper_1905_00661_b300.testing as hetm_testing
 from roundkit import bits_of, check_keys, flags_of, gpu_bitmaps, submit, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -225,8 +226,8 @@ def test_validation_planted(hetm, torch, n_log):
     with h.Context(1 << 20, v.granule_bytes) as ctx:
         ctx.load(v.init)
         first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
-        ctx.gpu_mark(torch.from_numpy(first).cuda())
-        ctx.gpu_mark(torch.from_numpy(v.plant_addr).cuda(), torch.from_numpy(v.plant_value).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(first).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(v.plant_addr).cuda(), torch.from_numpy(v.plant_value).cuda())
         ref0 = oracle.round_planted(v.init, v.read_granules, v.plant_addr, v.plant_value,
                                     log, v.granule_bytes)
         rs_bits, ws_bits = gpu_bitmaps(ctx, h)
@@ -241,7 +242,7 @@ def test_log_shipped_by_concurrent_threads(hetm, torch):
     with h.Context(1 << 20, v.granule_bytes, {"cpu_threads": 4, "log_chunk_bytes": 4800}) as ctx:
         ctx.load(v.init)
         first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
-        ctx.gpu_mark(torch.from_numpy(first).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(first).cuda())
         ref0 = oracle.round_planted(v.init, v.read_granules, v.plant_addr[:0], v.plant_value[:0],
                                     v.log, v.granule_bytes)
         _finish_round(ctx, h, torch, v.init, ref0.replayed, ref0.R, v.log, v.granule_bytes,
@@ -318,7 +319,7 @@ def test_validate_only_leaves_state(hetm, torch):
     with h.Context(1 << 18, v.granule_bytes) as ctx:
         ctx.load(v.init)
         first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
-        ctx.gpu_mark(torch.from_numpy(first).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(first).cuda())
         dlog = to_dev(torch, v.log)
         flags = torch.zeros((len(v.log) + 31) // 32, dtype=torch.int32, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")

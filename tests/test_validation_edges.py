@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 import workloads as wl
+import paper_1905_00661_b300.testing as hetm_testing
 from roundkit import flags_of, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -34,7 +35,7 @@ def _validate_only(h, torch, ctx, log):
 
 def _mark_read(ctx, torch, v):
     first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
-    ctx.gpu_mark(torch.from_numpy(first).cuda())
+    hetm_testing.gpu_mark(ctx, torch.from_numpy(first).cuda())
 
 
 def test_dense_read_set_bypasses_filter(hetm, torch):

@@ -20,6 +20,7 @@ import pytest
 
 import oracle
 import workloads as wl
+import paper_1905_00661_b300.testing as hetm_testing
 from roundkit import flags_of, to_dev
 
 
@@ -40,7 +41,7 @@ def test_noalloc_matches_validate_only_on_two_calls(hetm):
     n_words = 1 << 20
     with h.Context(n_words, v.granule_bytes) as ctx:
         first = (v.read_granules.astype(np.uint64) * (v.granule_bytes // 4)).astype(np.uint32)
-        ctx.gpu_mark(torch.from_numpy(first).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(first).cuda())
         rs = ctx.device_tensor(h.RS_BMP)
         dlog = to_dev(torch, v.log)
         stream = ctx.stream
@@ -80,7 +81,7 @@ def test_noalloc_edge_cases(hetm):
     log["addr"][bad] = n_words + np.arange(bad.size, dtype=np.uint32)
     with h.Context(n_words, G) as ctx:
         first = (v.read_granules.astype(np.uint64) * (G // 4)).astype(np.uint32)
-        ctx.gpu_mark(torch.from_numpy(first).cuda())
+        hetm_testing.gpu_mark(ctx, torch.from_numpy(first).cuda())
         rs = ctx.device_tensor(h.RS_BMP)
         stream = ctx.stream
         for n in (0, 1, 31, 127, 128, 129, len(log)):
