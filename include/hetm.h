@@ -466,11 +466,21 @@ typedef struct hetm_request {
     uint32_t txid_base, word_base;
 } hetm_request;
 
+/* Admission: a waiting batch is admitted (in arrival order) when its device
+ * footprint (records + order + status + outputs) fits the device memory free
+ * at that moment, as cudaMemGetInfo reports it, less free_reserve -- memory
+ * that other allocations take after the server started is seen -- and, when
+ * device_budget is set, when the bytes of admitted batches stay within it.
+ * A batch that does not fit while no batch is in flight completes with
+ * HETM_ENOMEM (counted in `refused`); otherwise it waits for in-flight
+ * batches to finish. */
 typedef struct hetm_server_config {
     int32_t per_batch;           /* 1: one round per batch (the plain form)        */
     uint32_t max_round_batches;  /* batches per round; 1024                        */
     uint64_t max_round_tx;       /* transactions per round; 1<<22                  */
-    uint64_t device_budget;      /* bytes for in-flight batches; 0 = half of free  */
+    uint64_t device_budget;      /* fixed cap on in-flight batch bytes; 0 = none    */
+    uint64_t free_reserve;       /* device bytes admission leaves free; 0 = 1/16 of
+                                    the device's memory                          */
 } hetm_server_config;
 
 typedef struct hetm_server_stats {
@@ -483,8 +493,9 @@ typedef struct hetm_server hetm_server;
 HETM_API int hetm_server_config_default(hetm_server_config *cfg);
 /* Start the loop thread.  The context must outlive the server. */
 HETM_API int hetm_server_create(hetm_server **out, hetm_ctx *ctx, const hetm_server_config *cfg);
-/* Queue a batch (thread-safe).  HETM_EBUSY if it can never fit the budget
- * or the round capacity.  The host buffers must stay valid until wait. */
+/* Queue a batch (thread-safe).  HETM_EBUSY if it can never fit (larger than
+ * device_budget, or than the device's memory less free_reserve) or exceeds
+ * the round capacity.  The host buffers must stay valid until wait. */
 HETM_API int hetm_server_submit(hetm_server *s, const hetm_request *r, uint64_t *id);
 /* Block until batch `id` completed (bounded: HETM_ETIMEOUT after 120 s). */
 HETM_API int hetm_server_wait(hetm_server *s, uint64_t id, double *latency_ms);

@@ -117,7 +117,7 @@ class hetm_request(ctypes.Structure):
 
 class hetm_server_config(ctypes.Structure):
     _fields_ = [("per_batch", _i32), ("max_round_batches", _u32), ("max_round_tx", _u64),
-                ("device_budget", _u64)]
+                ("device_budget", _u64), ("free_reserve", _u64)]
 
 
 class hetm_server_stats(ctypes.Structure):
@@ -561,13 +561,14 @@ class Server:
     caller keeps alive until ``wait``; ``per_batch`` selects one round per batch."""
 
     def __init__(self, ctx: Context, per_batch=False, max_round_batches=1024,
-                 max_round_tx=1 << 22, device_budget=0):
+                 max_round_tx=1 << 22, device_budget=0, free_reserve=0):
         cfg = hetm_server_config()
         _ck(_lib.hetm_server_config_default(ctypes.byref(cfg)), "hetm_server_config_default")
         cfg.per_batch = int(per_batch)
         cfg.max_round_batches = max_round_batches
         cfg.max_round_tx = max_round_tx
         cfg.device_budget = device_budget
+        cfg.free_reserve = free_reserve
         self.ctx = ctx
         self.h = _vp()
         ctx.torch.cuda.synchronize()

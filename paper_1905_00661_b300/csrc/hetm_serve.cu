@@ -73,7 +73,8 @@ struct hetm_server {
     uint64_t next_id = 1;
     bool stop = false;
     std::thread loop;
-    size_t budget = 0, held = 0;
+    size_t budget = 0, held = 0;  // budget 0: admission follows free device memory only
+    size_t reserve = 0;           // device memory admission always leaves free
     // stats
     uint64_t rounds = 0, completed = 0, committed = 0, refused = 0;
     std::vector<double> lat;
@@ -209,22 +210,50 @@ void complete_round(hetm_server *s, std::vector<Req *> &group, int rc, cudaEvent
     finish(s, group, rc);
 }
 
-// Admit waiting batches (arrival order) under the budget and capacities.
+// Device memory free for batches now: what the device reports free (memory
+// other allocations took since the server started counts against it), less
+// the reserve.  Batches of earlier groups are already allocated when the
+// loop admits the next group, so they are part of what is not free.
+size_t free_for_batches(const hetm_server *s) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+    return free_b > s->reserve ? free_b - s->reserve : 0;
+}
+
+// Admit waiting batches (arrival order) while their device footprint fits
+// the memory free now (and the optional fixed budget) and the round's
+// capacities.  A batch that does not fit while nothing is in flight cannot
+// be admitted by waiting: it fails with HETM_ENOMEM (into `refused`).
 // With `block`, wait until at least one batch is waiting (or stop).
-bool admit(hetm_server *s, std::vector<Req *> &group, bool block) {
+bool admit(hetm_server *s, std::vector<Req *> &group, bool block, std::vector<Req *> &refused) {
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (block) s->cv_in.wait(lk, [&] { return s->stop || !s->waiting.empty(); });
+        if (s->waiting.empty()) return !s->stop;
+    }
+    const size_t avail = free_for_batches(s);
     std::unique_lock<std::mutex> lk(s->mu);
-    if (block) s->cv_in.wait(lk, [&] { return s->stop || !s->waiting.empty(); });
-    if (s->waiting.empty()) return !s->stop;
     uint64_t tx = 0;
+    size_t taken = 0;
     while (!s->waiting.empty()) {
         Req *q = s->waiting.front();
         const size_t f = footprint(q->r);
         if (!group.empty() && (s->cfg.per_batch || group.size() >= s->cfg.max_round_batches ||
                                tx + q->r.n_tx > s->cfg.max_round_tx))
             break;
-        if (s->held + f > s->budget) break;  // wait for in-flight batches to free memory
+        const bool fits = taken + f <= avail && (s->budget == 0 || s->held + f <= s->budget);
+        if (!fits) {
+            if (group.empty() && s->held == 0) {  // nothing in flight will free memory
+                s->waiting.pop_front();
+                ++s->refused;
+                refused.push_back(q);
+                continue;
+            }
+            break;  // wait for in-flight batches to free memory
+        }
         s->waiting.pop_front();
         s->held += f;
+        taken += f;
         tx += q->r.n_tx;
         group.push_back(q);
     }
@@ -246,10 +275,19 @@ void loop_main(hetm_server *s) {
     std::vector<Req *> cur;  // launched, not completed
     int cur_rc = HETM_OK;
     int ev = 0;  // s->rdone[ev]: the end of cur's result copies
+    std::vector<Req *> refused;
+    auto fail_refused = [&] {
+        if (refused.empty()) return;
+        for (Req *q : refused) q->dev_bytes = 0;  // never allocated
+        finish(s, refused, HETM_ENOMEM);
+        refused.clear();
+    };
     for (;;) {
         if (cur.empty()) {  // nothing in flight: wait for work
             std::vector<Req *> g;
-            if (!admit(s, g, true)) return;
+            const bool go = admit(s, g, true, refused);
+            fail_refused();
+            if (!go) return;
             if (g.empty()) {
                 std::this_thread::sleep_for(std::chrono::microseconds(20));
                 continue;
@@ -268,7 +306,8 @@ void loop_main(hetm_server *s) {
         }
         std::vector<Req *> next;
         int next_rc = HETM_OK;
-        admit(s, next, false);
+        admit(s, next, false, refused);
+        fail_refused();
         bool next_open = false;
         if (!next.empty()) {
             next_rc = stage_group(s, next);
@@ -322,7 +361,8 @@ int hetm_server_create(hetm_server **out, hetm_ctx *ctx, const hetm_server_confi
         delete s;
         return HETM_ECUDA;
     }
-    s->budget = d.device_budget ? d.device_budget : free_b / 2;
+    s->budget = d.device_budget;
+    s->reserve = d.free_reserve ? d.free_reserve : total_b / 16;
     s->main = static_cast<cudaStream_t>(hetm_ctx_stream(ctx));
     if (cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->rdone[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -355,8 +395,14 @@ int hetm_server_submit(hetm_server *s, const hetm_request *r, uint64_t *id) {
     if (!q) return HETM_ENOMEM;
     q->r = *r;
     q->arrival = Clock::now();
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        delete q;
+        return HETM_ECUDA;
+    }
     std::lock_guard<std::mutex> g(s->mu);
-    if (footprint(*r) > s->budget || r->n_tx > s->cfg.max_round_tx) {
+    const size_t f = footprint(*r);
+    if ((s->budget && f > s->budget) || f + s->reserve > total_b || r->n_tx > s->cfg.max_round_tx) {
         ++s->refused;
         delete q;
         return HETM_EBUSY;

@@ -127,3 +127,38 @@ def test_admission_by_device_budget(hetm):
         for i in range(len(banks)):
             lo = bank_base + i * RANGE
             assert oracle.sum64(final[lo:lo + RANGE]) == 1000 * RANGE
+
+
+def test_admission_follows_free_device_memory(hetm):
+    """Admission reads the device's free memory at every admission, so memory
+    taken by another allocation after the server started is seen: with
+    admission leaving all but ~600 MB free, a 48 MB batch is served; once a
+    1 GB tensor is allocated beside the server the same batch no longer fits
+    (nothing is in flight to free memory: it completes with HETM_ENOMEM);
+    after the tensor is released it is served again."""
+    import torch
+    h = hetm
+    lay, bank_base, start, cfg, banks, cache = _setup()
+    tx = wl.bank_transfers(8, (wl.S.SRC, wl.S.DST, wl.S.AMT), 1 << 21, 0, RANGE)  # ~48 MB on device
+    with h.Context(len(start), 64, cfg) as ctx:
+        ctx.load(start)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free, _ = torch.cuda.mem_get_info()
+        reserve = free - (600 << 20)
+        with h.Server(ctx, free_reserve=reserve) as srv:
+            srv.wait(srv.submit(h.HETM_WL_BANK, tx, word_base=bank_base))
+            hog = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            bid = srv.submit(h.HETM_WL_BANK, tx, word_base=bank_base)
+            with pytest.raises(h.HetmError) as e:
+                srv.wait(bid)
+            assert e.value.code == h.HETM_ENOMEM
+            del hog
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            srv.wait(srv.submit(h.HETM_WL_BANK, tx, word_base=bank_base))
+            st = srv.stats()
+        assert st["refused"] == 1
+        final = ctx.read_stmr(h.STMR_W)
+        assert oracle.sum64(final[bank_base:bank_base + RANGE]) == 1000 * RANGE
