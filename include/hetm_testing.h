@@ -9,7 +9,8 @@
  *   hetm_gpu_mark             -- in libhetm.so (it needs the context)
  *   hetm_handoff_latency,
  *   hetm_random_access_rate,
- *   hetm_l2_probe_rate        -- in libhetm_testing.so
+ *   hetm_l2_probe_rate,
+ *   hetm_log_stream_time      -- in libhetm_testing.so
  *
  * Same conventions as hetm.h: 0 = HETM_OK, negative HETM_E* on error.
  */
@@ -68,6 +69,16 @@ HETM_API int hetm_random_access_rate(uint32_t log2_words, uint64_t n_access, dou
  * filter.  Allocates and frees the array; synchronous. */
 HETM_API int hetm_l2_probe_rate(uint32_t log2_words, uint64_t n_probe, uint32_t smem_bytes,
                                 double *per_s);
+
+/* The log stream of validation alone: the address field of each of the n
+ * tuples of dev_log (device, 16-byte aligned) read with the validation
+ * kernel's loads and launch shape (one 1024-thread CTA per SM holding
+ * smem_bytes of shared memory), nothing else done.  *seconds = mean of 10
+ * launches after a warm-up (CUDA events), a 256 MiB buffer written before
+ * each so that the log does not start in L2.  Allocates 256 MiB for the
+ * call; synchronous. */
+HETM_API int hetm_log_stream_time(const hetm_log_entry *dev_log, uint64_t n, uint32_t smem_bytes,
+                                  double *seconds);
 
 #ifdef __cplusplus
 }

@@ -144,10 +144,85 @@ __global__ void __launch_bounds__(1024, 1) k_l2_probe(const uint32_t *__restrict
     }
 }
 
+// The log stream of the validation kernel alone: every tuple's address field
+// read with the kernel's loads (4 bytes of every 12, one 32-tuple group per
+// warp instruction, 4 groups in flight per warp) and nothing else.
+__global__ void __launch_bounds__(1024, 1) k_log_stream(const uint32_t *__restrict__ lw, uint64_t n,
+                                                       uint32_t *sink) {
+    extern __shared__ uint32_t s_hold2[];  // occupancy only
+    constexpr int U = 4;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = (gridDim.x * (uint64_t)blockDim.x) >> 5;
+    const uint64_t n_groups = (n + 31) / 32;
+    const uint64_t g0 = warp * n_groups / n_warps, g1 = (warp + 1) * n_groups / n_warps;
+    uint32_t acc = 0;
+    for (uint64_t g = g0; g < g1; g += U) {
+        uint32_t a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t t = (g + u) * 32 + lane;
+            uint32_t v = 0;
+            if (g + u < g1 && t < n)
+                asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(lw + 3 * t));
+            a[u] = v;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc += __ballot_sync(kFull, a[u] & 1u);
+    }
+    if (acc == 0x12345678u) {
+        s_hold2[threadIdx.x] = acc;
+        *sink = s_hold2[threadIdx.x];
+    }
+}
+
 }  // namespace
 }  // namespace hetm
 
 using namespace hetm;
+
+extern "C" int hetm_log_stream_time(const hetm_log_entry *dev_log, uint64_t n, uint32_t smem_bytes,
+                                    double *seconds) {
+    if (!dev_log || n == 0 || smem_bytes > 200u * 1024 || !seconds) return HETM_EINVAL;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return HETM_ECUDA;
+    uint32_t *sink = nullptr;
+    void *flush = nullptr;  // written between launches: more than L2 holds
+    const size_t flush_bytes = 256ull << 20;
+    if (cudaMalloc(&sink, 64) != cudaSuccess) return HETM_ENOMEM;
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaFree(sink);
+        return HETM_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_log_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    double total = 0;
+    const int reps = 10;
+    for (int rep = 0; e == cudaSuccess && rep <= reps; ++rep) {  // the first launch warms up
+        float ms = 0;
+        e = cudaMemsetAsync(flush, rep & 0xFF, flush_bytes);
+        if (e == cudaSuccess) e = cudaEventRecord(e0);
+        if (e == cudaSuccess) {
+            k_log_stream<<<n_sm, 1024, smem_bytes>>>(reinterpret_cast<const uint32_t *>(dev_log), n, sink);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep) total += ms * 1e-3;
+    }
+    if (e == cudaSuccess) *seconds = total / reps;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    cudaFree(flush);
+    return e == cudaSuccess ? HETM_OK : HETM_ECUDA;
+}
 
 extern "C" int hetm_l2_probe_rate(uint32_t log2_words, uint64_t n_probe, uint32_t smem_bytes,
                                   double *per_s) {

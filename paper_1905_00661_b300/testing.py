@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libhetm_tes
 #: every symbol include/hetm_testing.h declares, and the library that exports it
 SYMBOLS = {"hetm_gpu_mark": "libhetm.so", "hetm_handoff_latency": "libhetm_testing.so",
            "hetm_random_access_rate": "libhetm_testing.so",
-           "hetm_l2_probe_rate": "libhetm_testing.so"}
+           "hetm_l2_probe_rate": "libhetm_testing.so",
+           "hetm_log_stream_time": "libhetm_testing.so"}
 
 _D = ctypes.POINTER(ctypes.c_double)
 _lib.hetm_gpu_mark.restype, _lib.hetm_gpu_mark.argtypes = _int, [_vp, _vp, _vp, _u64]
@@ -39,6 +40,7 @@ def lib():
         L.hetm_handoff_latency.restype, L.hetm_handoff_latency.argtypes = _int, [_u32, _D, _D]
         L.hetm_random_access_rate.restype, L.hetm_random_access_rate.argtypes = _int, [_u32, _u64, _D, _D]
         L.hetm_l2_probe_rate.restype, L.hetm_l2_probe_rate.argtypes = _int, [_u32, _u64, _u32, _D]
+        L.hetm_log_stream_time.restype, L.hetm_log_stream_time.argtypes = _int, [_vp, _u64, _u32, _D]
         _tl = L
     return _tl
 
@@ -72,4 +74,13 @@ def l2_probe_rate(log2_words=19, n_probe=1 << 24, smem_bytes=128 * 1024):
     r = ctypes.c_double()
     _ck(lib().hetm_l2_probe_rate(int(log2_words), int(n_probe), int(smem_bytes), ctypes.byref(r)),
         "hetm_l2_probe_rate")
+    return r.value
+
+
+def log_stream_time(dev_log, n, smem_bytes=128 * 1024):
+    """Seconds for the validation kernel's log stream alone over n tuples of a
+    device log (hetm_log_stream_time)."""
+    r = ctypes.c_double()
+    _ck(lib().hetm_log_stream_time(_ptr(dev_log), int(n), int(smem_bytes), ctypes.byref(r)),
+        "hetm_log_stream_time")
     return r.value

@@ -32,7 +32,8 @@ def test_library_exports_every_declared_symbol():
     for name, where in t.SYMBOLS.items():
         assert hasattr(libs[where], name), name
     # the probes are not part of the round library
-    for name in ("hetm_handoff_latency", "hetm_random_access_rate", "hetm_l2_probe_rate"):
+    for name in ("hetm_handoff_latency", "hetm_random_access_rate", "hetm_l2_probe_rate",
+                 "hetm_log_stream_time"):
         assert not hasattr(L, name), name
 
 
@@ -95,6 +96,7 @@ def test_random_access_probe_rejects_bad_arguments_without_gpu():
     r = ctypes.c_double()
     assert t.lib().hetm_l2_probe_rate(9, 100, 0, ctypes.byref(r)) == h.HETM_EINVAL
     assert t.lib().hetm_l2_probe_rate(19, 100, 300 * 1024, ctypes.byref(r)) == h.HETM_EINVAL
+    assert t.lib().hetm_log_stream_time(None, 100, 0, ctypes.byref(r)) == h.HETM_EINVAL
     assert t.lib().hetm_random_access_rate(10, 100, ctypes.byref(r), None) == h.HETM_EINVAL
     assert t.lib().hetm_random_access_rate(24, 0, ctypes.byref(r), None) == h.HETM_EINVAL
     assert t.lib().hetm_random_access_rate(24, 100, None, None) == h.HETM_EINVAL
