@@ -869,6 +869,22 @@ def run_case(name):
                 ms.append(st["ms_exec"])
         print(json.dumps({"case": name, "committed": st["committed"], "ms_exec": ms, "rc": st["rc"]}))
         return st["rc"]
+    if name == "w2_small":  # W2 (40 reads), 2^18 transactions, 50% updates, 2^26 words, optimistic STM
+        log2w = 26
+        init = wl.init_stmr(SEED, 1 << log2w)
+        tx = wl.w2_batch(seed=SEED, batch=3, n_tx=1 << 18, log2_words=log2w, update_frac=0.5)
+        cfg = {"cpu_threads": 1, "exec_mode": 1, "exec_threads": 256, "lock_log2": 24}
+        with h.Context(1 << log2w, 1024, cfg) as ctx:
+            ctx.load(init)
+            dtx = torch.from_numpy(tx.view(np.uint8)).cuda()
+            o = torch.empty(len(tx), dtype=torch.int64, device="cuda")
+            st_ = torch.empty(len(tx), dtype=torch.uint8, device="cuda")
+            out = torch.empty(len(tx), dtype=torch.int32, device="cuda")
+            ctx.submit_batch(h.HETM_WL_W2, dtx, o, st_, out, n_tx=len(tx))
+            st = ctx.round(stats=True)
+        print(json.dumps({"case": name, "committed": st["committed"], "ms_exec": st["ms_exec"],
+                          "aborts": st["aborts"], "rc": st["rc"]}))
+        return st["rc"] if st["committed"] == len(tx) else 1
     if name == "validate_small":  # validation-at-scale log (16M tuples) on a 2^27-word STMR
         v = wl.validation_round(seed=1, log2_words=27, granule_bytes=32, with_init=False)
         with h.Context(1 << 27, 32, {"log_capacity": 1 << 12, "exec_mode": 1}) as ctx:
