@@ -951,11 +951,22 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             else if (ext & (1u << k)) w = &sm.ext[k][t];
             watch[k] = (uint32_t)__cvta_generic_to_shared(w);
         }
+        // what the pass needs, worked out once: every instruction in the pass
+        // is on the path of each hand-on inside a warp
+        const uint32_t gt = g + 1;
+        uint32_t pubmask = 0;
+        uint32_t pturn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            pturn[k] = (rc.turn[k] & kTurnMask) + 1u;
+            if (k < (int)n && (rc.turn[k] & kFPublish)) pubmask |= 1u << k;
+        }
+        const int32_t aux0 = (int32_t)rc.aux;
         auto run_tx = [&]() {
             if (rmw4) {
-                sum = cur[0] + cur[1] + cur[2] + cur[3];
+                sum = (cur[0] + cur[1]) + (cur[2] + cur[3]);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) nv[k] = sum + k + (int32_t)rc.aux;
+                for (int k = 0; k < 4; ++k) nv[k] = sum + (aux0 + k);
             } else if (wl == HETM_WL_RMW) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -983,26 +994,50 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 if (k < (int)n) *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (k < (int)n && (rc.turn[k] & kFPublish))
-                    st_rlx64(o.packed + rc.res[k],
-                             ((unsigned long long)((rc.turn[k] & kTurnMask) + 1) << 32) | (uint32_t)nv[k]);
+                if (pubmask & (1u << k))
+                    st_rlx64(o.packed + rc.res[k], ((unsigned long long)pturn[k] << 32) | (uint32_t)nv[k]);
             finished = true;
             executed = true;
         };
+        const bool all_rmw4 = __all_sync(kFull, rmw4 || finished);
         uint32_t idle = 0, checks = 0;
         for (;;) {
             unsigned long long v[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v[k]) : "r"(watch[k]) : "memory");
+            // a watched cell tagged with this segment holds the slot's input; a
+            // slot that is not pending watches this lane's own output, tagged
+            // only once the lane has run, so its value is never taken
+            uint32_t gotm = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const bool got = ((pend >> k) & 1u) && (uint32_t)(v[k] >> 32) == g + 1;
+                const bool got = (uint32_t)(v[k] >> 32) == gt;
                 cur[k] = got ? (int32_t)(uint32_t)v[k] : cur[k];
-                pend &= got ? ~(1u << k) : ~0u;
+                gotm |= got ? (1u << k) : 0u;
             }
-            const bool ready = !finished && pend == 0;
-            if (ready) run_tx();
+            const bool ready = !finished && (pend & ~gotm) == 0;
+            if (all_rmw4) {
+                // every lane a 4-word W1 update (or none): the body straight,
+                // its stores predicated on `ready`
+                const int32_t s4 = (cur[0] + cur[1]) + (cur[2] + cur[3]);
+                if (ready) {
+                    sum = s4;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        nv[k] = s4 + (aux0 + k);
+                        *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (pubmask & (1u << k))
+                            st_rlx64(o.packed + rc.res[k], ((unsigned long long)pturn[k] << 32) | (uint32_t)nv[k]);
+                    finished = true;
+                    executed = true;
+                }
+            } else if (ready) {
+                run_tx();
+            }
             __syncwarp();
             if (__all_sync(kFull, finished)) break;
             if (__any_sync(kFull, ready)) {
