@@ -938,8 +938,9 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         bool timed_out = false;
         // Each slot still pending watches one shared word: its predecessor's
         // output slot in this segment, or its external input from the poll
-        // warp; a slot no longer pending watches this lane's own output
-        // (never tagged before the lane runs).  One pass is four
+        // warp; a slot no longer pending watches this lane's own output cell
+        // (never tagged before the lane runs; written only for slots whose
+        // next access is in this segment).  One pass is four
         // independent shared loads and selects, with no per-slot branching,
         // so that a hand-on inside the segment costs one short pass.
         uint32_t watch[4];
@@ -962,6 +963,13 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             if (k < (int)n && (rc.turn[k] & kFPublish)) pubmask |= 1u << k;
         }
         const int32_t aux0 = (int32_t)rc.aux;
+        // slots whose next access is in this segment: only those hand on through
+        // shared memory (the W1 body below stores those alone: a shared store
+        // in the pass lengthens every hand-on; the general body stores all)
+        uint32_t locmask = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < (int)n && !(rc.turn[k] & (kFLast | kFPublish))) locmask |= 1u << k;
         auto run_tx = [&]() {
             if (rmw4) {
                 sum = (cur[0] + cur[1]) + (cur[2] + cur[3]);
@@ -1007,8 +1015,9 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             for (int k = 0; k < 4; ++k)
                 asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v[k]) : "r"(watch[k]) : "memory");
             // a watched cell tagged with this segment holds the slot's input; a
-            // slot that is not pending watches this lane's own output, tagged
-            // only once the lane has run, so its value is never taken
+            // slot that is not pending watches this lane's own output cell,
+            // tagged (if at all) only once the lane has run, so its value is
+            // never taken
             uint32_t gotm = 0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -1026,7 +1035,8 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         nv[k] = s4 + (aux0 + k);
-                        *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
+                        if (locmask & (1u << k))
+                            *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
