@@ -95,8 +95,6 @@ struct hetm_ctx {
     uint64_t *d_prefix = nullptr;
     uint64_t *d_prefix0 = nullptr; // {0} for single-batch launches
     hetm_log_entry *dlog[2] = {nullptr, nullptr};
-    uint32_t *marks = nullptr;     // validation -> apply: a bit per tuple that may be newest
-    uint64_t marks_cap = 0;        //   tuples it covers
 
     // pinned staging of the batch table: two stagings per round (batches at
     // its start, the CPU log after the execution phase is launched), for two
@@ -422,18 +420,14 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
 // first and applies only when no tuple hit (both passes read the count).
 int enqueue_validate_apply(hetm_ctx *c, uint32_t *flags, cudaEvent_t *e) {
     const bool cpu_loses = c->cfg.conflict_policy == HETM_POLICY_CPU_LOSES;
-    // GPU-loses: the fused TS pass marks the tuples that may be their word's
-    // newest, and the apply reads TS again for those only
     CK(launch_validate(c->d_round, c->rs, c->gshift, c->n_words, flags, &c->scr->conflicts,
-                       cpu_loses ? nullptr : c->TS, &c->scr->err, c->filter, c->n_sm, c->stream,
-                       cpu_loses ? nullptr : c->marks, c->marks_cap));
+                       cpu_loses ? nullptr : c->TS, &c->scr->err, c->filter, c->n_sm, c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
     if (cpu_loses)
         CK(launch_ts_max_if_clean(c->d_round, c->TS, c->n_words, &c->scr->conflicts, c->stream_blocks,
                                   c->stream));
     CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream,
-                    cpu_loses ? &c->scr->conflicts : nullptr, cpu_loses ? nullptr : c->marks,
-                    c->marks_cap));
+                    cpu_loses ? &c->scr->conflicts : nullptr));
     return HETM_OK;
 }
 
@@ -656,10 +650,8 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         !dev_alloc_t(c, &c->scr, 1) || !dev_alloc_t(c, &c->d_round, nb + 1) ||
         !dev_alloc_t(c, &c->d_batches, nb) || !dev_alloc_t(c, &c->d_prefix, nb + 1) ||
         !dev_alloc_t(c, &c->d_prefix0, 2) || !dev_alloc_t(c, &c->dlog[0], d.log_capacity) ||
-        !dev_alloc_t(c, &c->dlog[1], d.log_capacity) ||
-        !dev_alloc_t(c, &c->marks, d.log_capacity / 32 + 1))
+        !dev_alloc_t(c, &c->dlog[1], d.log_capacity))
         return fail(HETM_ENOMEM);
-    c->marks_cap = (d.log_capacity / 32 + 1) * 32;
     // optimistic executor: the list of indices its read-only phase leaves to
     // the STM (rounds above max_round_tx transactions go unlisted)
     if (d.exec_mode == HETM_EXEC_OPTIMISTIC && d.max_round_tx && d.max_round_tx <= (1ull << 32) &&

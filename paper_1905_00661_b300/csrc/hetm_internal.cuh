@@ -240,21 +240,17 @@ cudaError_t launch_watch(const hetm_log_entry *log, uint64_t n, const uint32_t *
                          uint64_t n_words, unsigned int *stop, const unsigned int *segs_done,
                          const unsigned int *segs_total, const unsigned int *exec_over,
                          unsigned long long budget_ns, int blocks, cudaStream_t s);
-// ts non-null: also the first apply pass (TS max), and with marks (may be
-// null) a bit per tuple that may be its word's newest, for logs of at most
-// marks_cap tuples (read by launch_apply)
 cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
                             uint64_t n_words, uint32_t *flags, unsigned long long *count,
                             uint32_t *ts, int *err, const uint32_t *filter, int blocks,
-                            cudaStream_t s, uint32_t *marks = nullptr, uint64_t marks_cap = 0);
+                            cudaStream_t s);
 cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const uint32_t *rs,
                                    uint32_t gshift, uint64_t n_words, uint32_t *flags,
                                    unsigned long long *count, int *err, const uint32_t *filter,
                                    int blocks, cudaStream_t s);
 cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int32_t *S,
                          uint64_t n_words, int blocks, cudaStream_t s,
-                         const unsigned long long *skip_if = nullptr, const uint32_t *marks = nullptr,
-                         uint64_t marks_cap = 0);
+                         const unsigned long long *skip_if = nullptr);
 cudaError_t launch_ts_max_if_clean(const DevRound *rp, uint32_t *ts, uint64_t n_words,
                                    const unsigned long long *conflicts, int blocks, cudaStream_t s);
 // err (may be null): a kErrTimeout there undoes the batch (S -> W) whatever

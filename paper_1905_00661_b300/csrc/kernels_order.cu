@@ -28,6 +28,8 @@
 // budget; transactions are handed out in index order to resident warps, so
 // the lowest unfinished transaction can always run.
 
+#include <type_traits>
+
 #include "hetm_internal.cuh"
 
 namespace hetm {
@@ -964,8 +966,8 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
         }
         const int32_t aux0 = (int32_t)rc.aux;
         // slots whose next access is in this segment: only those hand on through
-        // shared memory (the W1 body below stores those alone: a shared store
-        // in the pass lengthens every hand-on; the general body stores all)
+        // shared memory, and only those are stored (a shared store in the pass
+        // lengthens every hand-on)
         uint32_t locmask = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
@@ -999,7 +1001,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (k < (int)n) *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
+                if (locmask & (1u << k)) *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (pubmask & (1u << k))
@@ -1008,63 +1010,70 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
             executed = true;
         };
         const bool all_rmw4 = __all_sync(kFull, rmw4 || finished);
-        uint32_t idle = 0, checks = 0;
-        for (;;) {
-            unsigned long long v[4];
+        // The pass loop, compiled twice: for a warp whose lanes are all 4-word
+        // W1 updates (or none) a loop of its own with the straight body, for
+        // every other warp the general one.
+        auto passes = [&](auto w1_only) {
+            constexpr bool kW1 = decltype(w1_only)::value;
+            uint32_t idle = 0, checks = 0;
+            for (;;) {
+                unsigned long long v[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v[k]) : "r"(watch[k]) : "memory");
-            // a watched cell tagged with this segment holds the slot's input; a
-            // slot that is not pending watches this lane's own output cell,
-            // tagged (if at all) only once the lane has run, so its value is
-            // never taken
-            uint32_t gotm = 0;
+                for (int k = 0; k < 4; ++k)
+                    asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v[k]) : "r"(watch[k]) : "memory");
+                // a watched cell tagged with this segment holds the slot's input; a
+                // slot that is not pending watches this lane's own output cell,
+                // tagged (if at all) only once the lane has run, so its value is
+                // never taken
+                uint32_t gotm = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const bool got = (uint32_t)(v[k] >> 32) == gt;
-                cur[k] = got ? (int32_t)(uint32_t)v[k] : cur[k];
-                gotm |= got ? (1u << k) : 0u;
-            }
-            const bool ready = !finished && (pend & ~gotm) == 0;
-            if (all_rmw4) {
-                // every lane a 4-word W1 update (or none): the body straight,
-                // its stores predicated on `ready`
-                const int32_t s4 = (cur[0] + cur[1]) + (cur[2] + cur[3]);
-                if (ready) {
-                    sum = s4;
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        nv[k] = s4 + (aux0 + k);
-                        if (locmask & (1u << k))
-                            *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (pubmask & (1u << k))
-                            st_rlx64(o.packed + rc.res[k], ((unsigned long long)pturn[k] << 32) | (uint32_t)nv[k]);
-                    finished = true;
-                    executed = true;
+                for (int k = 0; k < 4; ++k) {
+                    const bool got = (uint32_t)(v[k] >> 32) == gt;
+                    cur[k] = got ? (int32_t)(uint32_t)v[k] : cur[k];
+                    gotm |= got ? (1u << k) : 0u;
                 }
-            } else if (ready) {
-                run_tx();
-            }
-            __syncwarp();
-            if (__all_sync(kFull, finished)) break;
-            if (__any_sync(kFull, ready)) {
+                const bool ready = !finished && (pend & ~gotm) == 0;
+                if constexpr (kW1) {
+                    const int32_t s4 = (cur[0] + cur[1]) + (cur[2] + cur[3]);
+                    if (ready) {
+                        sum = s4;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            nv[k] = s4 + (aux0 + k);
+                            if (locmask & (1u << k))
+                                *(volatile unsigned long long *)&sm.pack[k][t] = tag | (uint32_t)nv[k];
+                        }
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (pubmask & (1u << k))
+                                st_rlx64(o.packed + rc.res[k],
+                                         ((unsigned long long)pturn[k] << 32) | (uint32_t)nv[k]);
+                        finished = true;
+                        executed = true;
+                    }
+                } else {
+                    if (ready) run_tx();
+                }
+                __syncwarp();
+                if (__all_sync(kFull, finished)) break;
+                if (__any_sync(kFull, ready)) {
+                    idle = 0;
+                    continue;
+                }
+                // an idle pass leaves the issue slots to the warps that can run
+                if (HETM_IDLE_SLEEP_NS) __nanosleep(HETM_IDLE_SLEEP_NS);
+                if (++idle < HETM_IDLE_PASSES) continue;
                 idle = 0;
-                continue;
+                if (__any_sync(kFull, *(volatile int *)&sm.abort != 0) ||
+                    ((++checks & 3u) == 0 &&
+                     __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns)) {
+                    timed_out = true;
+                    break;
+                }
             }
-            // an idle pass leaves the issue slots to the warps that can run
-            if (HETM_IDLE_SLEEP_NS) __nanosleep(HETM_IDLE_SLEEP_NS);
-            if (++idle < HETM_IDLE_PASSES) continue;
-            idle = 0;
-            if (__any_sync(kFull, *(volatile int *)&sm.abort != 0) ||
-                ((++checks & 3u) == 0 &&
-                 __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns)) {
-                timed_out = true;
-                break;
-            }
-        }
+        };
+        if (all_rmw4) passes(std::true_type{});
+        else passes(std::false_type{});
         if (executed) {
             const unsigned long long key = 2ull * (v0 + 1 + rc.u);
             if (!cache) {

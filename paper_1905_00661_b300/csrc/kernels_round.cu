@@ -128,8 +128,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
                                               const uint32_t *__restrict__ rs, uint32_t gshift,
                                               uint64_t n_words, uint32_t *__restrict__ flags,
                                               unsigned long long *count, uint32_t *ts, int *err,
-                                              const uint32_t *filter, uint32_t *s_filter,
-                                              uint32_t *marks = nullptr) {
+                                              const uint32_t *filter, uint32_t *s_filter) {
     constexpr int U = kValGroups;
     const uint32_t *lw = reinterpret_cast<const uint32_t *>(log);  // 3 words per tuple
     const unsigned lane = threadIdx.x & 31u;
@@ -182,18 +181,6 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (seen[u] < s[u]) atomicMax(ts + a[u], s[u]);
-            // A tuple whose timestamp is not above a value TS already held
-            // cannot be its word's newest (timestamps are unique per word):
-            // the apply pass reads TS again only for the tuples marked here.
-            if (marks) {
-                uint32_t mine_m = 0;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t b = __ballot_sync(kFull, seen[u] < s[u]);
-                    if (lane == (unsigned)u) mine_m = b;
-                }
-                if (lane < (unsigned)U && g + lane < g1) marks[g + lane] = mine_m;
-            }
         }
         uint32_t mine = 0;
 #pragma unroll
@@ -216,20 +203,16 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
     if (lane == 0 && hits && count) atomicAdd(count, (unsigned long long)hits);
 }
 
-// marks (kMax only, may be null): one bit per tuple, bit-packed like the
-// flags, for logs of at most marks_cap tuples
 template <bool kMax>
 __global__ void __launch_bounds__(kValThreads, 1) k_validate_round(const DevRound *rp, const uint32_t *rs,
                                                                    uint32_t gshift, uint64_t n_words,
                                                                    uint32_t *flags,
                                                                    unsigned long long *count,
                                                                    uint32_t *ts, int *err,
-                                                                   const uint32_t *filter, uint32_t *marks,
-                                                                   uint64_t marks_cap) {
+                                                                   const uint32_t *filter) {
     extern __shared__ uint4 s_dyn[];  // the filter
-    const uint64_t n = rp->n_log;
-    validate_body<kMax>(rp->log, n, rs, gshift, n_words, flags, count, ts, err, filter,
-                        reinterpret_cast<uint32_t *>(s_dyn), kMax && n <= marks_cap ? marks : nullptr);
+    validate_body<kMax>(rp->log, rp->n_log, rs, gshift, n_words, flags, count, ts, err, filter,
+                        reinterpret_cast<uint32_t *>(s_dyn));
 }
 
 __global__ void __launch_bounds__(kValThreads, 1) k_validate_direct(const hetm_log_entry *log, uint64_t n,
@@ -307,19 +290,14 @@ __global__ void __launch_bounds__(256) k_ts_max_if_clean(const DevRound *rp, uin
 }
 
 // skip_if (may be null): the round's conflict count; a nonzero count skips
-// the apply (CPU-loses policy).  marks (may be null; used for logs of at most
-// marks_cap tuples): the validation pass's bit per tuple, clear for a tuple
-// that cannot be its word's newest -- such a tuple neither reads TS again
-// nor writes.
+// the apply (CPU-loses policy).
 __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_t *__restrict__ ts,
                                                int32_t *__restrict__ W, int32_t *__restrict__ S,
-                                               uint64_t n_words, const unsigned long long *skip_if,
-                                               const uint32_t *__restrict__ marks, uint64_t marks_cap) {
+                                               uint64_t n_words, const unsigned long long *skip_if) {
     if (skip_if && *(volatile const unsigned long long *)skip_if) return;
     __shared__ uint4 s_stage[256 / 32 * kTileVec];
     const hetm_log_entry *log = rp->log;
     const uint64_t n = rp->n_log;
-    const uint32_t *mk = n <= marks_cap ? marks : nullptr;
     const unsigned lane = threadIdx.x & 31u;
     uint4 *stage = s_stage + (threadIdx.x >> 5) * kTileVec;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -334,12 +312,9 @@ __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_
         uint32_t a[4], s[4];
         int32_t v[4];
         tile_fields(cur, a, v, s);
-        // lane l holds tuples 4l..4l+3 of the tile: bits (4l & 31)..+3 of its
-        // group's mark word (group l / 8 of the tile's four)
-        const uint32_t mw = mk ? (__ldg(mk + c * 4 + (lane >> 3)) >> ((lane & 7u) * 4)) : 0xFu;
         uint32_t t[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) t[j] = a[j] < n_words && ((mw >> j) & 1u) ? __ldcg(ts + a[j]) : 0u;
+        for (int j = 0; j < 4; ++j) t[j] = a[j] < n_words ? __ldcg(ts + a[j]) : 0u;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (a[j] < n_words && t[j] == s[j]) {
@@ -471,14 +446,14 @@ cudaError_t validate_setup() {
 cudaError_t launch_validate(const DevRound *rp, const uint32_t *rs, uint32_t gshift,
                             uint64_t n_words, uint32_t *flags, unsigned long long *count,
                             uint32_t *ts, int *err, const uint32_t *filter, int blocks,
-                            cudaStream_t s, uint32_t *marks, uint64_t marks_cap) {
+                            cudaStream_t s) {
     const size_t smem = kValSmem;
     if (ts)
         k_validate_round<true><<<blocks, kValThreads, smem, s>>>(rp, rs, gshift, n_words, flags, count,
-                                                                 ts, err, filter, marks, marks_cap);
+                                                                 ts, err, filter);
     else
         k_validate_round<false><<<blocks, kValThreads, smem, s>>>(rp, rs, gshift, n_words, flags, count,
-                                                                  ts, err, filter, nullptr, 0);
+                                                                  ts, err, filter);
     return cudaGetLastError();
 }
 
@@ -503,9 +478,8 @@ cudaError_t launch_validate_direct(const hetm_log_entry *log, uint64_t n, const 
 
 cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int32_t *S,
                          uint64_t n_words, int blocks, cudaStream_t s,
-                         const unsigned long long *skip_if, const uint32_t *marks,
-                         uint64_t marks_cap) {
-    k_apply<<<blocks, 256, 0, s>>>(rp, ts, W, S, n_words, skip_if, marks, marks_cap);
+                         const unsigned long long *skip_if) {
+    k_apply<<<blocks, 256, 0, s>>>(rp, ts, W, S, n_words, skip_if);
     return cudaGetLastError();
 }
 
