@@ -703,14 +703,14 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int l) {
 // each one over through shared memory as soon as it is satisfied.  A warp
 // none of whose lanes ran in a pass sleeps briefly, leaving the issue slots
 // to the warps at the front of the chains.  (Measured on the 4M-transaction
-// Zipf(0.99) batch: 50 ns after each idle pass is a few percent faster than
-// spinning; longer sleeps, or sleeps scaled by an estimate of the turns still
-// ahead, are no better.)
+// Zipf(0.99) batch: 20 ns after each idle pass is 1-2% faster than 50 or
+// 100 ns and a few percent faster than spinning; sleeps scaled by an estimate
+// of the turns still ahead are no better.)
 #ifndef HETM_SLEEP_PER_TURN
 #define HETM_SLEEP_PER_TURN 32  // poll warp: ns of sleep per turn still ahead of its nearest wait
 #endif
 #ifndef HETM_IDLE_SLEEP_NS
-#define HETM_IDLE_SLEEP_NS 50  // ns of sleep after a pass in which no lane of the warp ran
+#define HETM_IDLE_SLEEP_NS 20  // ns of sleep after a pass in which no lane of the warp ran
 #endif
 #ifndef HETM_IDLE_PASSES
 #define HETM_IDLE_PASSES 4  // idle passes between two looks at the abort flag and the clock
