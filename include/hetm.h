@@ -348,7 +348,10 @@ typedef struct hetm_round_stats {
     uint64_t n_log;          /* CPU tuples validated                     */
     uint64_t n_conflicts;    /* tuples that hit RS_bmp                    */
     int32_t conflict;        /* 1: GPU batch undone                       */
-    int32_t err;             /* HETM_OK or HETM_EDEVICE                   */
+    int32_t err;             /* HETM_OK; HETM_ETIMEOUT when the execution
+                                phase ran out of its budget (the batch was
+                                undone), whatever else went wrong; else
+                                HETM_EDEVICE after an out-of-range address */
     uint64_t committed;      /* GPU transactions committed this round     */
     uint64_t gave_up;        /* GPU transactions that gave up             */
     uint64_t aborts;         /* aborted GPU attempts this round           */
