@@ -97,9 +97,12 @@ typedef struct hetm_rmw_tx {
  * bit 0 set it also writes s + j + txid to its j-th word for j = 0..3 (the
  * update transactions of both workloads update 4 positions).  The 40 words
  * of one transaction must be distinct.  176 bytes (16-byte multiple).
- * W2 runs under HETM_EXEC_OPTIMISTIC (read-only transactions in its
- * read-only phase, updates under the STM with validated reads); a context
- * in ordered mode refuses W2 batches (HETM_EINVAL at submission). */
+ * Read-only W2 transactions run in either executor's read-only phase
+ * (lock-free, on the launch-start state).  Updates run under the STM with
+ * their 36 read-only words validated against a clock snapshot: in
+ * HETM_EXEC_OPTIMISTIC with the launch's other updates, in
+ * HETM_EXEC_ORDERED after the ordered phase, serialized after every other
+ * transaction of the launch. */
 typedef struct hetm_w2_tx {
     uint32_t addr[40];
     uint32_t flags;

@@ -43,6 +43,7 @@ struct Scratch {                    // device-resident counters
     unsigned int exec_over;         //   nonzero once every executor kernel has finished
     unsigned long long v0;          // optimistic executor: commit clock before the launch
     unsigned long long rest_n;      //   indices the read-only phase left to the STM
+    unsigned long long w2n;         // ordered executor: W2 updates listed for the STM tail
 };
 
 struct RoundOut {                   // pinned copy of the round's results
@@ -179,6 +180,8 @@ struct hetm_ctx {
 
     OrderArgs ord{};               // ordered-executor scratch (exec_mode ORDERED)
     uint32_t *rest = nullptr;      // optimistic executor: indices left by the read-only phase
+    uint32_t *w2list = nullptr;    // ordered executor: the W2 updates of a launch
+    int tail_blocks = 0;           //   grid of the STM that runs them after the ordered phase
     int ord_blocks = 0;
     int exec_blocks = 0, exec_threads = 256, stream_blocks = 0;
     unsigned long long prev_counters[3] = {0, 0, 0};
@@ -362,6 +365,22 @@ ExecArgs exec_args(hetm_ctx *c, const DevRound *rp, const DevBatch *batches,
     return a;
 }
 
+// Ordered mode: the W2 updates of the launch (listed by the ordering pre-pass)
+// run under the STM after the ordered phase, serialized after every
+// transaction of the launch (the pre-pass took the clock past the launch's
+// versions); a launch without W2 updates draws nothing and ends at once.
+cudaError_t launch_w2_tail(hetm_ctx *c, ExecArgs e) {
+    e.skip_ro = 1;
+    e.rest = c->w2list;
+    e.rest_n = &c->scr->w2n;
+    e.rest_cap = ~0ull;
+    e.stop = nullptr;
+    e.segs_done = e.segs_total = nullptr;
+    cudaError_t err = cudaMemsetAsync(&c->scr->next, 0, sizeof(unsigned long long), c->stream);
+    if (err == cudaSuccess) err = launch_exec(e, c->tail_blocks, 256, c->stream);
+    return err;
+}
+
 // Executor launch(es) for the staged table: one persistent launch over all
 // batches, or one launch per batch.
 // `capturing`: recorded into g_exec, which then marks (ev_watch_start) the
@@ -376,8 +395,10 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
                 if (capturing)
                     CK(cudaEventRecordWithFlags(c->ev_watch_start, c->stream, cudaEventRecordExternal));
             }
+            CK(cudaMemsetAsync(&c->scr->w2n, 0, sizeof(unsigned long long), c->stream));
             CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream, c->ro_side, c->ro_fork,
                               c->ro_join));
+            CK(launch_w2_tail(c, o.e));
             // stream order: set only after every kernel of the execution phase
             if (c->early) CK(cudaMemsetAsync(&c->scr->exec_over, 0xFF, sizeof(unsigned int), c->stream));
             return HETM_OK;
@@ -386,8 +407,10 @@ int enqueue_exec(hetm_ctx *c, bool per_batch, uint32_t nb, bool capturing = fals
             o.e = exec_args(c, c->d_round + 1 + b, c->d_batches + b, c->d_prefix0);
             o.e.stop = nullptr;  // no watcher runs beside per-batch launches
             o.e.segs_done = o.e.segs_total = nullptr;
+            CK(cudaMemsetAsync(&c->scr->w2n, 0, sizeof(unsigned long long), c->stream));
             CK(launch_ordered(o, c->ord_blocks, c->stream_blocks, c->stream, c->ro_side, c->ro_fork,
                               c->ro_join));
+            CK(launch_w2_tail(c, o.e));
         }
         return HETM_OK;
     }
@@ -677,6 +700,9 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         o.n_ord = o.n_acc + 1;
         o.n_tx32 = o.n_acc + 2;
         o.n_cache_runs = o.n_acc + 3;
+        if (!dev_alloc_t(c, &c->w2list, o.cap_tx)) return fail(HETM_ENOMEM);
+        o.w2list = c->w2list;
+        o.w2n = &c->scr->w2n;
     }
     for (auto &s : c->stage) {
         if (!host_alloc_t(&s.rounds, nb + 1) || !host_alloc_t(&s.batches, nb) ||
@@ -720,6 +746,9 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
     if (d.exec_mode == HETM_EXEC_ORDERED) {
         if (ordered_exec_occupancy(d.exec_threads, &occ) != 0 || occ < 1) occ = 1;
         c->ord_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ;
+        int tocc = 0;
+        if (exec_occupancy(256, &tocc) != 0 || tocc < 1) tocc = 1;
+        c->tail_blocks = c->n_sm * tocc;
     } else {
         if (exec_occupancy(c->exec_threads, &occ) != 0 || occ < 1) occ = 1;
         c->exec_blocks = d.exec_blocks ? (int)d.exec_blocks : c->n_sm * occ;
@@ -829,8 +858,6 @@ int hetm_gpu_submit_batch(hetm_ctx *c, const hetm_batch *b, uint64_t *batch_id) 
     if (!c || !b) return HETM_EINVAL;
     if (b->workload < HETM_WL_BANK || b->workload > HETM_WL_W2) return HETM_EINVAL;
     if (b->n_tx && !b->tx) return HETM_EINVAL;
-    // W2 (40 reads) runs under the optimistic executor only
-    if (b->workload == HETM_WL_W2 && c->cfg.exec_mode != HETM_EXEC_OPTIMISTIC) return HETM_EINVAL;
     if (b->workload == HETM_WL_CACHE) {
         const hetm_config &f = c->cfg;
         const uint64_t ns = 1ull << f.cache_log2_sets;

@@ -137,6 +137,10 @@ struct OrderArgs {
     unsigned long long *v0;     // commit clock before the launch
     uint32_t cap_tx, cap_acc, key_bits;
     uint32_t seg_log2;          // transactions per CTA segment = 2^seg_log2 (7, 8 or 9)
+    // W2 updates of the launch (null: none can occur), run under the STM
+    // after the ordered phase: w2list[0 .. *w2n)
+    uint32_t *w2list;
+    unsigned long long *w2n;
 };
 
 // ------------------------------------------------------------------ PTX helpers

@@ -296,6 +296,7 @@ struct TxView {
     uint32_t map;      // W1: 2-bit slot of the j-th declared word
     uint32_t aux;      // W1: txid; bank: amount
     const DevBatch *d;
+    bool tail;         // W2 update: runs under the STM after the ordered phase
 };
 
 __device__ __forceinline__ int find_batch(const uint64_t *prefix, uint32_t nb, uint64_t gi) {
@@ -316,6 +317,17 @@ __device__ __forceinline__ bool view_tx(const ExecArgs &a, uint64_t u, TxView &t
     t.wmask = 0;
     t.map = 0;
     t.aux = 0;
+    t.tail = false;
+    if (t.wl == HETM_WL_W2) {
+        // no resources here: read-only W2 transactions run in the read-only
+        // phase, updates under the STM after the ordered phase (40 words do
+        // not fit the ordered record)
+        const hetm_w2_tx *x = static_cast<const hetm_w2_tx *>(t.d->tx) + t.li;
+        bool ok = true;
+        for (int j = 0; j < 40; ++j) ok &= __ldg(&x->addr[j]) < a.n_words;
+        t.tail = (x->flags & 1u) != 0;
+        return ok;
+    }
     if (t.wl == HETM_WL_BANK) {
         const hetm_bank_tx x = static_cast<const hetm_bank_tx *>(t.d->tx)[t.li];
         t.addr[0] = t.d->word_base + x.src;
@@ -375,13 +387,27 @@ __global__ void __launch_bounds__(256) k_ord_count(OrderArgs o) {
         *a.gv = v0 + total + 1;  // this launch owns versions v0+1 .. v0+total+1
     }
     unsigned long long bad = 0;
-    for (uint64_t u = tid; u < total; u += stride) {
+    const unsigned lane = threadIdx.x & 31u;
+    // loop bound rounded up to whole warps: the W2 list is appended warp by warp
+    const uint64_t span = (total + 31) & ~31ull;
+    for (uint64_t u = tid; u < span; u += stride) {
         TxView t;
-        const bool ok = view_tx(a, u, t);
-        o.cnt[u] = ok && t.n ? (1ull << 32) | t.n : 0ull;
-        if (!ok) {  // out-of-range words or unknown workload: not executed
-            if (t.d->status) t.d->status[t.li] = kGaveUp;
-            ++bad;
+        bool ok = false, tail = false;
+        if (u < total) {
+            ok = view_tx(a, u, t);
+            o.cnt[u] = ok && t.n ? (1ull << 32) | t.n : 0ull;
+            if (!ok) {  // out-of-range words or unknown workload: not executed
+                if (t.d->status) t.d->status[t.li] = kGaveUp;
+                ++bad;
+            }
+            tail = ok && t.tail;
+        }
+        const unsigned m = __ballot_sync(kFull, tail);
+        if (m && o.w2list) {
+            unsigned long long base = 0;
+            if (lane == (unsigned)(__ffs(m) - 1)) base = atomicAdd(o.w2n, (unsigned long long)__popc(m));
+            base = __shfl_sync(kFull, base, __ffs(m) - 1);
+            if (tail) o.w2list[base + __popc(m & lanemask_lt())] = (uint32_t)u;
         }
     }
     if (bad) {

@@ -1,15 +1,18 @@
 """W2 (40 reads, Sec. V-A) and the uninstrumented executor, against the oracle
 (needs a GPU).
 
-* W2 batches under the optimistic executor (read-only transactions in the
-  read-only phase, updates under the STM with reads validated against a
-  clock snapshot): STMR^W after execution equals the serial replay in the
-  GPU's reported commit order, every committed sum equals the replay's, and
-  RS_bmp / WS_bmp equal the replay's granule and chunk sets.  A small STMR
-  makes the 40-word read sets collide often, so validation failures and
-  retries are exercised; then a whole round (CPU log, validation, merge)
-  against the oracle's final state.
-* A context in ordered mode refuses W2 batches.
+* W2 batches under both executors (read-only transactions in the read-only
+  phase, updates under the STM with reads validated against a clock
+  snapshot -- with the launch's other updates in optimistic mode, after the
+  ordered phase in ordered mode): STMR^W after execution equals the serial
+  replay in the GPU's reported commit order, every committed sum equals the
+  replay's, and RS_bmp / WS_bmp equal the replay's granule and chunk sets.
+  A small STMR makes the 40-word read sets collide often, so validation
+  failures and retries are exercised; then a whole round (CPU log,
+  validation, merge) against the oracle's final state.
+* In ordered mode, W2 mixed with W1 updates in one launch: the W2 updates
+  commit after every W1 transaction of the launch, and the replay of both in
+  the reported order reproduces STMR^W.
 * uninstrumented = 1 (what Sec. V-A measures instrumentation costs against):
   the same transactions give the same STMR^W and outputs, and RS_bmp and
   WS_bmp stay empty.
@@ -44,15 +47,16 @@ def _exec(ctx, h, torch, batches):
     return keys, stat, out
 
 
+@pytest.mark.parametrize("mode", [1, 0])
 @pytest.mark.parametrize("log2w,n_tx,upd", [(16, 30000, 0.1), (16, 30000, 0.9), (12, 6000, 0.5)])
-def test_w2_matches_the_oracle(hetm, torch, log2w, n_tx, upd):
+def test_w2_matches_the_oracle(hetm, torch, log2w, n_tx, upd, mode):
     h = hetm
     n = 1 << log2w
     start = wl.init_words(41, 0, n)
     # two uneven batches in one launch (txid bases continue across them)
     tx = wl.w2_batch(seed=41, batch=0, n_tx=n_tx, log2_words=log2w, update_frac=upd)
     cut = n_tx // 3
-    with h.Context(n, G, {"exec_mode": 1, "ws_chunk_bytes": C, "cpu_threads": 1}) as ctx:
+    with h.Context(n, G, {"exec_mode": mode, "ws_chunk_bytes": C, "cpu_threads": 1}) as ctx:
         ctx.load(start)
         b0 = submit(ctx, torch, wl.WORKLOAD_W2, tx[:cut], txid_base=100)
         b1 = submit(ctx, torch, wl.WORKLOAD_W2, tx[cut:], txid_base=100 + cut)
@@ -81,16 +85,44 @@ def test_w2_matches_the_oracle(hetm, torch, log2w, n_tx, upd):
             assert ctx.exec_counters()["aborts"] > 0  # the contended case retried
 
 
-def test_ordered_mode_refuses_w2(hetm, torch):
+def test_ordered_mode_runs_w2_after_its_ordered_phase(hetm, torch):
     h = hetm
-    tx = wl.w2_batch(seed=43, batch=0, n_tx=64, log2_words=12)
-    with h.Context(1 << 12, G, {"exec_mode": 0, "cpu_threads": 1}) as ctx:
-        with pytest.raises(h.HetmError) as e:
-            submit(ctx, torch, wl.WORKLOAD_W2, tx)
-        assert e.value.code == h.HETM_EINVAL
+    n = 1 << 13
+    start = wl.init_words(45, 0, n)
+    w1 = wl.rmw_batch(seed=45, batch=0, n_tx=5000, log2_words=13, update_frac=0.5)
+    w2 = wl.w2_batch(seed=46, batch=0, n_tx=2000, log2_words=13, update_frac=0.5)
+    with h.Context(n, G, {"exec_mode": 0, "ws_chunk_bytes": C, "cpu_threads": 1}) as ctx:
+        ctx.load(start)
+        b1 = submit(ctx, torch, wl.WORKLOAD_RMW, w1, txid_base=0)
+        b2 = submit(ctx, torch, wl.WORKLOAD_W2, w2, txid_base=7)
+        k1, s1, o1 = _exec(ctx, h, torch, [b1])
+        k2, s2, o2 = b2.host()
+        assert (s1 == 1).all() and (s2 == 1).all()
+        upd1 = w1["flags"] == 1
+        upd2 = w2["flags"] == 1
+        # W2 updates after every W1 transaction; W2 read-only ones before every update
+        assert k2[upd2].min() > k1.max()
+        assert k2[~upd2].max() < k1[upd1].min()
+        # one history: replay both kinds merged by their commit keys
+        rep = start.copy()
+        order = np.argsort(np.concatenate([k1, k2]), kind="stable")
+        ref1, ref2 = np.zeros(len(w1), np.int32), np.zeros(len(w2), np.int32)
+        for i in order:
+            if i < len(w1):
+                one = w1[i:i + 1]
+                out, _, _ = oracle.replay_rmw(rep, one, [2], [1], G, C, txid_base=int(i))
+                ref1[i] = out[0]
+            else:
+                j = i - len(w1)
+                one = w2[j:j + 1]
+                out, _, _ = oracle.replay_w2(rep, one, [2], [1], G, C, txid_base=7 + int(j))
+                ref2[j] = out[0]
+        np.testing.assert_array_equal(o1, ref1)
+        np.testing.assert_array_equal(o2, ref2)
+        np.testing.assert_array_equal(ctx.read_stmr(h.STMR_W), rep)
 
 
-@pytest.mark.parametrize("mode,kind", [(1, "w1"), (1, "w2"), (0, "w1")])
+@pytest.mark.parametrize("mode,kind", [(1, "w1"), (1, "w2"), (0, "w1"), (0, "w2")])
 def test_uninstrumented_executor_records_nothing(hetm, torch, mode, kind):
     h = hetm
     n = 1 << 14
