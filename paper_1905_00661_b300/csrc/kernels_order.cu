@@ -731,10 +731,9 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int l) {
 // to the warps at the front of the chains.  (Measured on the 4M-transaction
 // Zipf(0.99) batch: 20 ns after each idle pass is 1-2% faster than 50 or
 // 100 ns and a few percent faster than spinning; sleeps scaled by an estimate
-// of the turns still ahead are no better.)
-#ifndef HETM_SLEEP_PER_TURN
-#define HETM_SLEEP_PER_TURN 32  // poll warp: ns of sleep per turn still ahead of its nearest wait
-#endif
+// of the turns still ahead are no better.  The poll warp itself does not
+// sleep: a sleep scaled by the turns still ahead of its nearest wait cost
+// 0.5%, and 10 ns a link on a chain inside one warp.)
 #ifndef HETM_IDLE_SLEEP_NS
 #define HETM_IDLE_SLEEP_NS 20  // ns of sleep after a pass in which no lane of the warp ran
 #endif
@@ -825,8 +824,7 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                 if ((++passes & 15u) == 0 &&
                     __shfl_sync(kFull, globaltimer_ns(), 0) - t0 > a.budget_ns)
                     break;  // the executors see the budget run out themselves
-                uint32_t kept = 0, min_gap = 0xFFFFFFFFu;
-                bool any_new = false;
+                uint32_t kept = 0;
                 for (uint32_t base = 0; base < n; base += 128) {
                     uint32_t sl[4], rs[4], tf[4];
                     unsigned long long pv[4];
@@ -848,14 +846,12 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                         if (sl[j] == 0xFFFFFFFFu) continue;
                         const uint32_t c = (uint32_t)(pv[j] >> 32), need = tf[j] & kTurnMask;
                         ok[j] = (tf[j] & kFWriter) ? c == need : c >= need;
-                        if (!ok[j]) min_gap = min(min_gap, need > c ? need - c : 1u);
                     }
                     // No fence before handing the inputs on: every pending input
                     // is a word whose value travels in the same 8-byte word as
                     // its turn count (cache requests do not run here), so the
                     // relaxed load above already holds everything the consumer
                     // reads.
-                    if (__any_sync(kFull, ok[0] || ok[1] || ok[2] || ok[3])) any_new = true;
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         if (ok[j])
@@ -879,11 +875,6 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                     __syncwarp();
                 }
                 n = kept;
-                if (n && !any_new) {
-                    const uint32_t mg = __reduce_min_sync(kFull, min_gap);
-                    if (HETM_SLEEP_PER_TURN && mg > 8 && mg != 0xFFFFFFFFu)
-                        __nanosleep(min(mg * (uint32_t)HETM_SLEEP_PER_TURN, 8000u));
-                }
             }
             __syncthreads();  // end of segment
             continue;
