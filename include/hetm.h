@@ -48,7 +48,10 @@ extern "C" {
 
 /* ---------------------------------------------------------------- errors */
 #define HETM_OK 0
-#define HETM_EINVAL (-1)    /* bad argument or precondition violated          */
+#define HETM_EINVAL (-1)    /* bad argument or precondition violated; from a
+                               round: a CPU tuple's ts out of range or
+                               repeated (hetm_log_entry), reported until
+                               hetm_load */
 #define HETM_ENOMEM (-2)    /* device or pinned host allocation failed        */
 #define HETM_ECAPACITY (-3) /* a fixed-capacity buffer or table is full       */
 #define HETM_ETIMEOUT (-4)  /* a bounded device wait gave up                  */
@@ -62,9 +65,16 @@ HETM_API const char *hetm_strerror(int code);
 
 /* --------------------------------------------------------------- records */
 /* CPU write-set log tuple (Sec. IV-B, CPU instrumentation).  12 bytes,
- * packed.  `ts` totally orders the writes to one word: it must be >= 1 and
- * unique per word over the lifetime of the context (ties and repeats are an
- * invalid input; which of two tied tuples wins is unspecified). */
+ * packed.  `ts` totally orders the writes to one word: 1 <= ts < 2^32 - 1
+ * and unique per word over the lifetime of the context (until hetm_load).
+ * A tuple is applied when its ts is the newest of its word.  The device
+ * checks the rule where it raises TS (under CPU_LOSES only in rounds that
+ * validate clean), and the round then reports HETM_EINVAL: for a ts out of
+ * range (the tuple is validated, not applied), and for a ts repeated on the
+ * newest ts of a word, within the round or from an earlier one (the word
+ * holds one of the values concerned; for a tie within the round W and S
+ * need not hold the same one).  A repeat below a word's newest ts changes
+ * nothing and may go unreported. */
 typedef struct hetm_log_entry {
     uint32_t addr;  /* word index into the STMR, < stmr_words */
     int32_t value;  /* value the CPU transaction wrote          */
@@ -354,7 +364,9 @@ typedef struct hetm_round_stats {
     int32_t err;             /* HETM_OK; HETM_ETIMEOUT when the execution
                                 phase ran out of its budget (the batch was
                                 undone), whatever else went wrong; else
-                                HETM_EDEVICE after an out-of-range address */
+                                HETM_EDEVICE after an out-of-range address;
+                                else HETM_EINVAL after a CPU timestamp out of
+                                range or repeated (hetm_log_entry) */
     uint64_t committed;      /* GPU transactions committed this round     */
     uint64_t gave_up;        /* GPU transactions that gave up             */
     uint64_t aborts;         /* aborted GPU attempts this round           */
@@ -629,7 +641,9 @@ HETM_API void hetm_dispatch_destroy(hetm_dispatch *d);
  * scratch context per candidate on the current device (3 x stmr_words x 4
  * bytes plus the executor's per-round state, freed after the candidate),
  * loads `init`, and times 1 + reps whole rounds (hetm_round) of the sample
- * batches (+ the CPU log), the first round untimed.
+ * batches (+ the CPU log), the first round untimed.  A round with the CPU
+ * log starts from `init` loaded again (a log's timestamps are applied once
+ * per context).
  *
  * Search, a coordinate search in three stages:
  *   0  executor shape -- every (mode, exec_threads, blocks per SM, lock_log2)

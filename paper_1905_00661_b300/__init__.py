@@ -238,6 +238,12 @@ def _ck(rc, what):
     return rc
 
 
+def _round_reported(rc, stats):
+    """A round call's code that its stats explain (the round ran): OK, or the
+    device error the round reports in ``err``."""
+    return rc == HETM_OK or (rc in (HETM_EDEVICE, HETM_ETIMEOUT, HETM_EINVAL) and rc == stats["err"])
+
+
 # ---------------------------------------------------------------------------
 # C-named wrappers
 # ---------------------------------------------------------------------------
@@ -527,7 +533,7 @@ class Context:
             self._leave()
             d = st.as_dict()
             d["rc"] = rc
-            if rc not in (HETM_OK, HETM_EDEVICE, HETM_ETIMEOUT):
+            if not _round_reported(rc, d):
                 raise HetmError(rc, "hetm_round")
             return d
         rc = _lib.hetm_round(self.h, None)
@@ -542,7 +548,7 @@ class Context:
         rc = _lib.hetm_round_wait(self.h, ctypes.byref(st))
         d = st.as_dict()
         d["rc"] = rc
-        if rc not in (HETM_OK, HETM_EDEVICE, HETM_ETIMEOUT):
+        if not _round_reported(rc, d):
             raise HetmError(rc, "hetm_round_wait")
         return d
 

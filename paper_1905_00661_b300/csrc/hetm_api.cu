@@ -447,8 +447,8 @@ int enqueue_validate_apply(hetm_ctx *c, uint32_t *flags, cudaEvent_t *e) {
                        cpu_loses ? nullptr : c->TS, &c->scr->err, c->filter, c->n_sm, c->stream));
     if (e) CK(cudaEventRecordWithFlags(e[1], c->stream, cudaEventRecordExternal));
     if (cpu_loses)
-        CK(launch_ts_max_if_clean(c->d_round, c->TS, c->n_words, &c->scr->conflicts, c->stream_blocks,
-                                  c->stream));
+        CK(launch_ts_max_if_clean(c->d_round, c->TS, c->n_words, &c->scr->conflicts, &c->scr->err,
+                                  c->stream_blocks, c->stream));
     CK(launch_apply(c->d_round, c->TS, c->W, c->S, c->n_words, c->stream_blocks, c->stream,
                     cpu_loses ? &c->scr->conflicts : nullptr));
     return HETM_OK;

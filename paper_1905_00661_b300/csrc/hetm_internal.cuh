@@ -50,12 +50,19 @@ struct DevRound {
 // error of the same or an earlier round).
 constexpr int kErrAddr = 1;
 constexpr int kErrTimeout = 2;
+constexpr int kErrLogTs = 4;  // a CPU tuple's timestamp out of range, or repeated
 
 // HETM_ETIMEOUT when the execution phase ran out of its budget (whatever else
-// went wrong), HETM_EDEVICE for any other device error, else HETM_OK.
+// went wrong), HETM_EDEVICE for an out-of-range address, HETM_EINVAL for a
+// CPU log that broke the timestamp rule, else HETM_OK.
 inline int err_code(int bits) {
-    return (bits & kErrTimeout) ? HETM_ETIMEOUT : (bits ? HETM_EDEVICE : HETM_OK);
+    if (bits & kErrTimeout) return HETM_ETIMEOUT;
+    if (bits & kErrAddr) return HETM_EDEVICE;
+    return bits ? HETM_EINVAL : HETM_OK;
 }
+
+// CPU timestamps are 1 .. 2^32 - 2 (0 is TS's "none yet").
+__host__ __device__ __forceinline__ bool ts_valid(uint32_t ts) { return ts - 1u < 0xFFFFFFFEu; }
 
 // Arguments of the executor kernel.
 struct ExecArgs {
@@ -256,7 +263,8 @@ cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int
                          uint64_t n_words, int blocks, cudaStream_t s,
                          const unsigned long long *skip_if = nullptr);
 cudaError_t launch_ts_max_if_clean(const DevRound *rp, uint32_t *ts, uint64_t n_words,
-                                   const unsigned long long *conflicts, int blocks, cudaStream_t s);
+                                   const unsigned long long *conflicts, int *err, int blocks,
+                                   cudaStream_t s);
 // err (may be null): a kErrTimeout there undoes the batch (S -> W) whatever
 // conflicts / force say
 cudaError_t launch_merge(const uint32_t *ws, uint32_t cshift, int32_t *W, int32_t *S,

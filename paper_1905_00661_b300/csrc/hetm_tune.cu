@@ -55,6 +55,9 @@ Outcome run_trial(uint64_t words, const int32_t *init, const hetm_batch *b, uint
     std::vector<float> ex, tot;
     std::vector<uint64_t> com;
     for (uint32_t r = 0; o.rc == HETM_OK && r <= reps; ++r) {
+        // a timestamp is applied once per word over a context's life, so a
+        // round that attaches the same log again starts from a fresh load
+        if (r && log && n_log) o.rc = hetm_load(c, init, words);
         for (uint32_t i = 0; o.rc == HETM_OK && i < nb; ++i) o.rc = hetm_gpu_submit_batch(c, b + i, nullptr);
         if (o.rc == HETM_OK && log && n_log) o.rc = hetm_log_attach(c, log, n_log);
         if (o.rc != HETM_OK) break;

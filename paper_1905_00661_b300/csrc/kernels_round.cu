@@ -87,18 +87,29 @@ __device__ __forceinline__ const uint32_t *load_filter(const uint32_t *filter, u
     return s_fill <= kFilterBits / 4 * 3 ? smem : nullptr;
 }
 
-// Raise TS[a] to s.  A skewed log sends many tuples to a few hot words, and
-// atomics on one word serialize in its L2 slice; a tuple whose timestamp is
-// not above the value seen through L1 cannot change TS and skips the atomic.
-// TS only grows during the pass, so a stale cached value is at most the
-// current one: a skip is always safe, at worst an atomic is not saved.
+// Raise TS[a] to timestamp s.  A skewed log sends many tuples to a few hot
+// words, and atomics on one word serialize in its L2 slice; a tuple whose
+// timestamp is not above the value seen through L1 cannot change TS and
+// skips the atomic.  TS only grows during the pass, so a stale cached value
+// is at most the current one: a skip is always safe, at worst an atomic is
+// not saved.
+//
+// The value a tuple sees (through L1, else returned by its atomic) is one
+// TS held, and when it equals s the timestamp is repeated: by another tuple
+// of the round or by one applied in an earlier round.  Of the tuples of one
+// word carrying its newest timestamp all but the first to reach L2 see s,
+// so a repeat of the timestamp the apply writes is always caught; a repeat
+// below it may go unseen and changes nothing.
 __device__ __forceinline__ uint32_t ts_seen(const uint32_t *ts, uint32_t a) {
     uint32_t seen;
     asm volatile("ld.global.ca.u32 %0, [%1];" : "=r"(seen) : "l"(ts + a));
     return seen;
 }
-__device__ __forceinline__ void ts_raise(uint32_t *ts, uint32_t a, uint32_t s) {
-    if (ts_seen(ts, a) < s) atomicMax(ts + a, s);
+// true when s repeats a timestamp TS holds for the word
+__device__ __forceinline__ bool ts_raise(uint32_t *ts, uint32_t a, uint32_t s) {
+    uint32_t seen = ts_seen(ts, a);
+    if (seen < s) seen = atomicMax(ts + a, s);
+    return seen == s;
 }
 
 // 4-byte load of a log field that is read once (no L1 allocation)
@@ -137,7 +148,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
     const uint64_t n_groups = (n + 31) / 32;
     const uint64_t g0 = warp * n_groups / n_warps, g1 = (warp + 1) * n_groups / n_warps;
     uint32_t hits = 0;
-    bool bad = false;
+    bool bad = false, bad_ts = false;
 
     uint32_t a[U], s[U];
     bool v[U];
@@ -166,6 +177,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
         for (int u = 0; u < U; ++u) {
             in[u] = v[u] && a[u] < n_words;
             bad |= v[u] && !in[u];
+            if (kMax) bad_ts |= in[u] && !ts_valid(s[u]);
             gr[u] = a[u] >> gshift;
             bool p = in[u];
             if (flt && p) {
@@ -174,13 +186,13 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
             }
             w[u] = p ? __ldg(rs + (gr[u] >> 5)) : 0u;
         }
+        uint32_t seen[U];
         if (kMax) {
-            uint32_t seen[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) seen[u] = in[u] ? ts_seen(ts, a[u]) : ~0u;
+            for (int u = 0; u < U; ++u) seen[u] = in[u] && ts_valid(s[u]) ? ts_seen(ts, a[u]) : ~0u;
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (seen[u] < s[u]) atomicMax(ts + a[u], s[u]);
+                if (seen[u] < s[u]) seen[u] = atomicMax(ts + a[u], s[u]);
         }
         uint32_t mine = 0;
 #pragma unroll
@@ -190,6 +202,11 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
         }
         hits += __popc(mine);
         if (flags && lane < (unsigned)U && g + lane < g1) flags[g + lane] = mine;
+        if (kMax) {  // the atomics' old values, read last (see ts_raise)
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                bad_ts |= in[u] && ts_valid(s[u]) && seen[u] == s[u];
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             a[u] = na[u];
@@ -198,6 +215,7 @@ __device__ __forceinline__ void validate_body(const hetm_log_entry *__restrict__
         }
     }
     if (bad) set_err(err, kErrAddr);
+    if (bad_ts) set_err(err, kErrLogTs);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(kFull, hits, o);
     if (lane == 0 && hits && count) atomicAdd(count, (unsigned long long)hits);
@@ -269,26 +287,31 @@ __global__ void __launch_bounds__(128) k_watch(const hetm_log_entry *__restrict_
     }
 }
 
-// Apply, second pass (Sec. IV-C): after TS holds the newest timestamp of
-// every logged word, exactly the tuple carrying it writes its value into
-// STMR^W and into the shadow STMR^S (Sec. IV-D: the shadow plus the CPU log
-// is the CPU's state).  Out-of-range tuples were reported by validation.
 // CPU-loses policy (Sec. IV-E): the CPU log is applied only when the whole
 // validation came back clean, so the TS max runs as its own pass after
 // validation and, like the apply, does nothing once a conflict was counted.
 __global__ void __launch_bounds__(256) k_ts_max_if_clean(const DevRound *rp, uint32_t *ts,
                                                          uint64_t n_words,
-                                                         const unsigned long long *conflicts) {
+                                                         const unsigned long long *conflicts,
+                                                         int *err) {
     if (*(volatile const unsigned long long *)conflicts) return;
     const hetm_log_entry *log = rp->log;
     const uint64_t n = rp->n_log;
     const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
+    bool bad_ts = false;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t a = __ldg(&log[i].addr);
-        if (a < n_words) ts_raise(ts, a, __ldg(&log[i].ts));
+        const uint32_t a = __ldg(&log[i].addr), s = __ldg(&log[i].ts);
+        if (a >= n_words) continue;
+        bad_ts |= !ts_valid(s) || ts_raise(ts, a, s);
     }
+    if (bad_ts) set_err(err, kErrLogTs);
 }
 
+// Apply, second pass (Sec. IV-C): after TS holds the newest timestamp of
+// every logged word, exactly the tuple carrying it writes its value into
+// STMR^W and into the shadow STMR^S (Sec. IV-D: the shadow plus the CPU log
+// is the CPU's state).  Out-of-range tuples were reported by validation,
+// timestamps out of range or repeated by the timestamp pass.
 // skip_if (may be null): the round's conflict count; a nonzero count skips
 // the apply (CPU-loses policy).
 __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_t *__restrict__ ts,
@@ -312,12 +335,16 @@ __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_
         uint32_t a[4], s[4];
         int32_t v[4];
         tile_fields(cur, a, v, s);
+        bool ok[4];
         uint32_t t[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) t[j] = a[j] < n_words ? __ldcg(ts + a[j]) : 0u;
+        for (int j = 0; j < 4; ++j) {
+            ok[j] = a[j] < n_words && ts_valid(s[j]);
+            t[j] = ok[j] ? __ldcg(ts + a[j]) : 0u;
+        }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (a[j] < n_words && t[j] == s[j]) {
+            if (ok[j] && t[j] == s[j]) {
                 W[a[j]] = v[j];
                 S[a[j]] = v[j];
             }
@@ -325,8 +352,8 @@ __global__ void __launch_bounds__(256) k_apply(const DevRound *rp, const uint32_
     }
     if (warp == n_warps - 1) {
         for (uint64_t i = n_tiles * 128 + lane; i < n; i += 32) {
-            uint32_t a = log[i].addr;
-            if (a < n_words && __ldcg(ts + a) == log[i].ts) {
+            const uint32_t a = log[i].addr, s = log[i].ts;
+            if (a < n_words && ts_valid(s) && __ldcg(ts + a) == s) {
                 W[a] = log[i].value;
                 S[a] = log[i].value;
             }
@@ -484,8 +511,9 @@ cudaError_t launch_apply(const DevRound *rp, const uint32_t *ts, int32_t *W, int
 }
 
 cudaError_t launch_ts_max_if_clean(const DevRound *rp, uint32_t *ts, uint64_t n_words,
-                                   const unsigned long long *conflicts, int blocks, cudaStream_t s) {
-    k_ts_max_if_clean<<<blocks, 256, 0, s>>>(rp, ts, n_words, conflicts);
+                                   const unsigned long long *conflicts, int *err, int blocks,
+                                   cudaStream_t s) {
+    k_ts_max_if_clean<<<blocks, 256, 0, s>>>(rp, ts, n_words, conflicts, err);
     return cudaGetLastError();
 }
 
