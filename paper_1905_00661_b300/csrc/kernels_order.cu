@@ -1072,11 +1072,13 @@ __global__ void __launch_bounds__(SEG + 32) k_seg_exec(OrderArgs o) {
                     if (ready) run_tx();
                 }
                 __syncwarp();
-                if (__all_sync(kFull, finished)) break;
+                // a pass in which a lane ran is followed by another: the warp
+                // leaves from an idle pass, so a busy pass takes one vote
                 if (__any_sync(kFull, ready)) {
                     idle = 0;
                     continue;
                 }
+                if (__all_sync(kFull, finished)) break;
                 // an idle pass leaves the issue slots to the warps that can run
                 if (HETM_IDLE_SLEEP_NS) __nanosleep(HETM_IDLE_SLEEP_NS);
                 if (++idle < HETM_IDLE_PASSES) continue;
