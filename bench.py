@@ -46,7 +46,7 @@ import workloads as wl  # noqa: E402
 # DRAM bytes (read + write) of the ordered-phase kernel per transaction of the
 # round, from one ncu capture of `bench.py --case rmw_small` (1M transactions,
 # 35.58 MB + 0.55 MB), scaled to a launch by the transaction count.
-TRAFFIC_SEG_EXEC_PER_TX = (35.580e6 + 0.547e6) / (1 << 20)
+TRAFFIC_SEG_EXEC_PER_TX = (35.532e6 + 0.670e6) / (1 << 20)
 # the main step's granule (the coarse bitmap of Sec. V-A) and merge chunk
 # (Sec. IV-D's 16 KB): part of the workload, the same in both arms
 MAIN_GRANULE = 1024
