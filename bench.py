@@ -45,7 +45,7 @@ import workloads as wl  # noqa: E402
 
 # DRAM bytes (read + write) of the ordered-phase kernel per transaction of the
 # round, from one ncu capture of `bench.py --case rmw_small` (1M transactions,
-# 35.58 MB + 0.55 MB), scaled to a launch by the transaction count.
+# 35.53 MB + 0.67 MB), scaled to a launch by the transaction count.
 TRAFFIC_SEG_EXEC_PER_TX = (35.532e6 + 0.670e6) / (1 << 20)
 # the main step's granule (the coarse bitmap of Sec. V-A) and merge chunk
 # (Sec. IV-D's 16 KB): part of the workload, the same in both arms
