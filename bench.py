@@ -530,7 +530,10 @@ def bench_host_merge(torch, h, inputs, tuned, rounds=6):
     chunks go to a pinned 2^28-word host replica.  Synchronously after each round
     (``read_dirty``) or double-buffered (Sec. IV-D, ``read_dirty_async``): the copy
     of round r overlaps the execution phase of round r+1, which reads and writes
-    STMR^W only.  Host wall time per round, both ways."""
+    STMR^W only.  Host wall time per round, both ways, and the device-timed
+    execution phase and round (CUDA events) beside it: with the copy in flight
+    their difference to the synchronous mode is what the copy's traffic costs
+    the executor; the rest of the wall time is the host's wait for the copy."""
     init, batches, logs = inputs
     dev_tx = torch.from_numpy(batches[0].view(np.uint8)).cuda()
     o = torch.empty(N_TX, dtype=torch.int64, device="cuda")
@@ -545,6 +548,7 @@ def bench_host_merge(torch, h, inputs, tuned, rounds=6):
             ctx.load(init)
             host.copy_(torch.from_numpy(init))
             nbytes = 0
+            ex, tot = [], []
             for r in range(rounds + 1):
                 if r == 1:
                     torch.cuda.synchronize()
@@ -554,6 +558,9 @@ def bench_host_merge(torch, h, inputs, tuned, rounds=6):
                                  txid_base=(r * N_TX) & 0xFFFFFFFF)
                 st = ctx.round(stats=True)
                 assert st["rc"] == h.HETM_OK and not st["conflict"]
+                if r:
+                    ex.append(st["ms_exec"])
+                    tot.append(st["ms_total"])
                 if mode == "sync":
                     _, b = ctx.read_dirty(host.numpy())
                 else:
@@ -562,6 +569,8 @@ def bench_host_merge(torch, h, inputs, tuned, rounds=6):
             ctx.read_dirty_wait()
             dt = time.perf_counter() - t0
             out[mode + "_ms_per_round"] = 1e3 * dt / rounds
+            out[mode + "_exec_ms"] = float(np.median(ex))
+            out[mode + "_round_device_ms"] = float(np.median(tot))
             out["dirty_bytes_per_round"] = nbytes / rounds
             half = (1 << LOG2W) // 2   # the GPU's half: the replica must equal W there
             w = ctx.read_stmr(h.STMR_W, 0, half)
