@@ -947,15 +947,20 @@ def run_case(name):
         # 2^18 W1 updates on 4 distinct words each; every `stride`-th one also
         # names word 0, so those form one chain of conflicting transactions whose
         # consecutive members are `stride` ranks apart: 1 = inside a warp,
-        # 32 = one warp apart, 512 = one 512-transaction segment (CTA) apart
+        # 32 = one warp apart, 512 = one 512-transaction segment (CTA) apart.
+        # The same batch without the chain (stride 0) gives the phase's fixed
+        # cost (ordering pre-pass, one pass over independent transactions),
+        # which is taken off before dividing by the links.
         n = 1 << 18
         log2w = 26
         i = np.arange(n, dtype=np.uint64)
         res = []
-        for stride in (1, 32, 512):
+        base_ms = None
+        for stride in (0, 1, 32, 512):
             tx = np.zeros(n, dtype=wl.RMW_DTYPE)
             a_ = ((1 << 20) + 16 + 4 * i[:, None] + np.arange(4, dtype=np.uint64)[None, :]).astype(np.uint32)
-            a_[(i % stride) == 0, 0] = 0
+            if stride:
+                a_[(i % stride) == 0, 0] = 0
             tx["addr"] = a_
             tx["flags"] = 1
             cfg = {"cpu_threads": 1, "max_round_tx": n, "exec_threads": 512}
@@ -973,10 +978,14 @@ def run_case(name):
                         return 1
                     if r:
                         ms.append(st["ms_exec"])
-            links = (n + stride - 1) // stride - 1
             t = float(np.median(ms))
-            res.append({"stride": stride, "links": links, "ms_exec": t, "ns_per_link": t * 1e6 / links})
-        print(json.dumps({"case": name, "chains": res}))
+            if not stride:
+                base_ms = t
+                continue
+            links = (n + stride - 1) // stride - 1
+            res.append({"stride": stride, "links": links, "ms_exec": t,
+                        "ns_per_link": (t - base_ms) * 1e6 / links})
+        print(json.dumps({"case": name, "ms_exec_without_chain": base_ms, "chains": res}))
         return 0
     raise SystemExit(f"unknown case {name}")
 
