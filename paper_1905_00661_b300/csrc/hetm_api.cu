@@ -694,12 +694,13 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
             !dev_alloc_t(c, &o.keys1, o.cap_acc) || !dev_alloc_t(c, &o.vals1, o.cap_acc) ||
             !dev_alloc_t(c, &o.hist, hist_n) || !dev_alloc_t(c, &o.runs, o.cap_acc) ||
             !dev_alloc_t(c, &o.rec, o.cap_tx) || !dev_alloc_t(c, &o.packed, o.cap_acc) ||
-            !dev_alloc_t(c, &o.n_acc, 4) || !dev_alloc_t(c, &o.cache_heads, o.cap_tx) ||
+            !dev_alloc_t(c, &o.n_acc, 5) || !dev_alloc_t(c, &o.cache_heads, o.cap_tx) ||
             !dev_alloc_t(c, &o.v0, 1))
             return fail(HETM_ENOMEM);
         o.n_ord = o.n_acc + 1;
         o.n_tx32 = o.n_acc + 2;
         o.n_cache_runs = o.n_acc + 3;
+        o.n_hist = o.n_acc + 4;
         if (!dev_alloc_t(c, &c->w2list, o.cap_tx)) return fail(HETM_ENOMEM);
         o.w2list = c->w2list;
         o.w2n = &c->scr->w2n;

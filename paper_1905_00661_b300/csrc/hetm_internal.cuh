@@ -139,6 +139,7 @@ struct OrderArgs {
     OrdRec *rec;                // [cap_tx] ordered-phase transactions by rank
     unsigned long long *packed; // [cap_acc] per resource: (turns done << 32) | value
     uint32_t *n_acc, *n_ord, *n_tx32;
+    uint32_t *n_hist;           // the radix sort's histogram length for the launch
     uint32_t *cache_heads;      // [cap_tx] first access of every cache set's run
     uint32_t *n_cache_runs;     //   their number
     unsigned long long *v0;     // commit clock before the launch

@@ -181,12 +181,17 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
 
-// hist[d * n_tiles_cap + tile] = count of digit d in the tile
+// hist[d * n_tiles + tile] = count of digit d in the tile, n_tiles = the
+// tiles the n (device) keys fill, so that the scan after it covers those
+// and not the capacity; *hist_n = 256 * n_tiles, the scan's count.
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *keys, const uint32_t *n_dev,
                                                              uint32_t shift, uint64_t *hist,
-                                                             uint32_t n_tiles_cap) {
+                                                             uint32_t *hist_n) {
     __shared__ uint32_t s_cnt[256];
     const uint32_t n = *n_dev;
+    const uint32_t n_tiles = (n + kSortTile - 1) / kSortTile;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *hist_n = 256u * n_tiles;
+    if (blockIdx.x >= n_tiles) return;
     const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
     s_cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -198,22 +203,22 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
         }
     }
     __syncthreads();
-    hist[(uint64_t)threadIdx.x * n_tiles_cap + blockIdx.x] = s_cnt[threadIdx.x];
+    hist[(uint64_t)threadIdx.x * n_tiles + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
 // Stable scatter: items keep their input order within a digit.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *kin, const uint32_t *vin,
                                                                 uint32_t *kout, uint32_t *vout,
                                                                 const uint32_t *n_dev, uint32_t shift,
-                                                                const uint64_t *hist_ex,
-                                                                uint32_t n_tiles_cap) {
+                                                                const uint64_t *hist_ex) {
     __shared__ uint32_t s_base[256];                      // running output position per digit
     __shared__ uint32_t s_wcnt[kSortThreads / 32][256];   // per-warp digit counts of a round
     const uint32_t n = *n_dev;
+    const uint32_t n_tiles = (n + kSortTile - 1) / kSortTile;
     const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
     if (base >= n) return;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    s_base[threadIdx.x] = (uint32_t)hist_ex[(uint64_t)threadIdx.x * n_tiles_cap + blockIdx.x];
+    s_base[threadIdx.x] = (uint32_t)hist_ex[(uint64_t)threadIdx.x * n_tiles + blockIdx.x];
     for (int r = 0; r < kSortItems; ++r) {
         for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][threadIdx.x] = 0;
         __syncthreads();
@@ -254,13 +259,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
 
 // Sort n (device) pairs by key, `bits` significant key bits, in place in
 // (k0, v0) using (k1, v1) as the other buffer.  hist holds 256 *
-// n_tiles_cap values; tot one value per scan tile of it.
+// n_tiles_cap values; tot one value per scan tile of it; hist_n one device
+// word (the histogram's length for the n at hand).
 static cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint32_t *n_dev, uint32_t cap, uint32_t bits, uint64_t *hist,
-                              uint64_t *tot, cudaStream_t s) {
+                              uint64_t *tot, uint32_t *hist_n, cudaStream_t s) {
     const uint32_t n_tiles_cap = (cap + kSortTile - 1) / kSortTile;
-    const uint32_t hist_n = 256u * n_tiles_cap;
-    const uint32_t scan_grid = (hist_n + kScanTile - 1) / kScanTile;
+    const uint32_t scan_grid = (256u * n_tiles_cap + kScanTile - 1) / kScanTile;
     uint32_t passes = (bits + 7) / 8;
     if (passes & 1u) ++passes;  // even pass count: the result lands back in (k0, v0)
     for (uint32_t p = 0; p < passes; ++p) {
@@ -274,11 +279,10 @@ static cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
             if (e != cudaSuccess) return e;
             continue;
         }
-        k_radix_hist<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, n_dev, shift, hist, n_tiles_cap);
-        cudaError_t e = device_scan<SumOp, true>(hist, hist, nullptr, hist_n, scan_grid, tot, 0, s);
+        k_radix_hist<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, n_dev, shift, hist, hist_n);
+        cudaError_t e = device_scan<SumOp, true>(hist, hist, hist_n, 0, scan_grid, tot, 0, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, hist,
-                                                             n_tiles_cap);
+        k_radix_scatter<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, hist);
     }
     return cudaGetLastError();
 }
@@ -1453,7 +1457,7 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
     if (e != cudaSuccess) return joined(e);
     k_ord_emit<<<stream_blocks, 256, 0, s>>>(o);
     e = radix_sort(o.keys0, o.vals0, o.keys1, o.vals1, o.n_acc, o.cap_acc, o.key_bits, o.hist,
-                   o.scan_tot, s);
+                   o.scan_tot, o.n_hist, s);
     if (e != cudaSuccess) return joined(e);
     k_ord_runs<<<stream_blocks, 256, 0, s>>>(o);
     const uint32_t acc_grid = (o.cap_acc + kScanTile - 1) / kScanTile;
