@@ -28,6 +28,7 @@
 // budget; transactions are handed out in index order to resident warps, so
 // the lowest unfinished transaction can always run.
 
+#include <algorithm>
 #include <type_traits>
 
 #include "hetm_internal.cuh"
@@ -86,9 +87,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint64_t *in,
                                                              uint64_t *tot, uint64_t identity) {
     __shared__ uint64_t s_warp[kScanThreads / 32];
     const uint32_t n = n_dev ? *n_dev : n_fix;
-    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-    if (base >= n) return;
+    const uint32_t nt = (n + kScanTile - 1) / kScanTile;
     Op op;
+    // a grid of the machine's size walks the tiles the count fills
+    for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const uint64_t base = (uint64_t)tile * kScanTile;
     uint64_t x[kScanItems];
     uint64_t run = identity;
 #pragma unroll
@@ -113,7 +116,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint64_t *in,
         if (i < n) out[i] = kExclusive ? acc : nxt;
         acc = nxt;
     }
-    if (threadIdx.x == kScanThreads - 1) tot[blockIdx.x] = incl;
+    if (threadIdx.x == kScanThreads - 1) tot[tile] = incl;
+    __syncthreads();  // s_warp is refilled by the next tile's scan
+    }
 }
 
 // Exclusive scan of the tile totals in place (one block, any count).
@@ -147,21 +152,24 @@ template <class Op>
 __global__ void __launch_bounds__(kScanThreads) k_scan_fix(uint64_t *out, const uint32_t *n_dev,
                                                            uint32_t n_fix, const uint64_t *tot) {
     const uint32_t n = n_dev ? *n_dev : n_fix;
-    const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
-    if (base >= n) return;
+    const uint32_t nt = (n + kScanTile - 1) / kScanTile;
     Op op;
-    const uint64_t c = tot[blockIdx.x];
+    for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        const uint64_t base = (uint64_t)tile * kScanTile;
+        const uint64_t c = tot[tile];
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const uint64_t i = base + k * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = op(c, out[i]);
+        for (int k = 0; k < kScanItems; ++k) {
+            const uint64_t i = base + k * kScanThreads + threadIdx.x;
+            if (i < n) out[i] = op(c, out[i]);
+        }
     }
 }
 
 }  // namespace
 
-// Device-wide scan of n (device or fixed) 64-bit values; `grid` covers the
-// capacity in tiles of kScanTile; tot holds one value per tile.
+// Device-wide scan of n (device or fixed) 64-bit values; `grid` blocks walk
+// the tiles of kScanTile (any grid works); tot holds one value per tile of
+// the capacity.
 template <class Op, bool kExclusive>
 static cudaError_t device_scan(const uint64_t *in, uint64_t *out, const uint32_t *n_dev,
                                uint32_t n_fix, uint32_t grid, uint64_t *tot, uint64_t identity,
@@ -191,19 +199,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t *key
     const uint32_t n = *n_dev;
     const uint32_t n_tiles = (n + kSortTile - 1) / kSortTile;
     if (blockIdx.x == 0 && threadIdx.x == 0) *hist_n = 256u * n_tiles;
-    if (blockIdx.x >= n_tiles) return;
-    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
-    s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    if (base < n) {
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint64_t base = (uint64_t)tile * kSortTile;
+        s_cnt[threadIdx.x] = 0;
+        __syncthreads();
 #pragma unroll
         for (int k = 0; k < kSortItems; ++k) {
             const uint64_t i = base + k * kSortThreads + threadIdx.x;
             if (i < n) atomicAdd(&s_cnt[(keys[i] >> shift) & 255u], 1u);
         }
+        __syncthreads();
+        hist[(uint64_t)threadIdx.x * n_tiles + tile] = s_cnt[threadIdx.x];
+        __syncthreads();  // s_cnt is cleared for the next tile
     }
-    __syncthreads();
-    hist[(uint64_t)threadIdx.x * n_tiles + blockIdx.x] = s_cnt[threadIdx.x];
 }
 
 // Stable scatter: items keep their input order within a digit.
@@ -215,10 +223,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     __shared__ uint32_t s_wcnt[kSortThreads / 32][256];   // per-warp digit counts of a round
     const uint32_t n = *n_dev;
     const uint32_t n_tiles = (n + kSortTile - 1) / kSortTile;
-    const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
-    if (base >= n) return;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    s_base[threadIdx.x] = (uint32_t)hist_ex[(uint64_t)threadIdx.x * n_tiles + blockIdx.x];
+    for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const uint64_t base = (uint64_t)tile * kSortTile;
+    s_base[threadIdx.x] = (uint32_t)hist_ex[(uint64_t)threadIdx.x * n_tiles + tile];
     for (int r = 0; r < kSortItems; ++r) {
         for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][threadIdx.x] = 0;
         __syncthreads();
@@ -253,6 +261,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
         s_base[threadIdx.x] += run;
         __syncthreads();
     }
+    }
 }
 
 }  // namespace
@@ -263,9 +272,12 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
 // word (the histogram's length for the n at hand).
 static cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1,
                               const uint32_t *n_dev, uint32_t cap, uint32_t bits, uint64_t *hist,
-                              uint64_t *tot, uint32_t *hist_n, cudaStream_t s) {
+                              uint64_t *tot, uint32_t *hist_n, uint32_t max_blocks, cudaStream_t s) {
     const uint32_t n_tiles_cap = (cap + kSortTile - 1) / kSortTile;
-    const uint32_t scan_grid = (256u * n_tiles_cap + kScanTile - 1) / kScanTile;
+    // grids of the machine's size that walk the tiles the keys fill
+    const uint32_t grid = std::max(1u, std::min(n_tiles_cap, max_blocks));
+    const uint32_t scan_grid =
+        std::max(1u, std::min((256u * n_tiles_cap + kScanTile - 1) / kScanTile, max_blocks));
     uint32_t passes = (bits + 7) / 8;
     if (passes & 1u) ++passes;  // even pass count: the result lands back in (k0, v0)
     for (uint32_t p = 0; p < passes; ++p) {
@@ -279,10 +291,10 @@ static cudaError_t radix_sort(uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t
             if (e != cudaSuccess) return e;
             continue;
         }
-        k_radix_hist<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, n_dev, shift, hist, hist_n);
+        k_radix_hist<<<grid, kSortThreads, 0, s>>>(ki, n_dev, shift, hist, hist_n);
         cudaError_t e = device_scan<SumOp, true>(hist, hist, hist_n, 0, scan_grid, tot, 0, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<n_tiles_cap, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, hist);
+        k_radix_scatter<<<grid, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_dev, shift, hist);
     }
     return cudaGetLastError();
 }
@@ -1452,15 +1464,16 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
         }
         return err;
     };
-    const uint32_t scan_grid = (o.cap_tx + kScanTile - 1) / kScanTile;
+    const uint32_t max_blocks = (uint32_t)std::max(stream_blocks, 1);
+    const uint32_t scan_grid = std::min((o.cap_tx + kScanTile - 1) / kScanTile, max_blocks);
     cudaError_t e = device_scan<SumOp, true>(o.cnt, o.cnt, o.n_tx32, 0, scan_grid, o.scan_tot, 0, s);
     if (e != cudaSuccess) return joined(e);
     k_ord_emit<<<stream_blocks, 256, 0, s>>>(o);
     e = radix_sort(o.keys0, o.vals0, o.keys1, o.vals1, o.n_acc, o.cap_acc, o.key_bits, o.hist,
-                   o.scan_tot, o.n_hist, s);
+                   o.scan_tot, o.n_hist, max_blocks, s);
     if (e != cudaSuccess) return joined(e);
     k_ord_runs<<<stream_blocks, 256, 0, s>>>(o);
-    const uint32_t acc_grid = (o.cap_acc + kScanTile - 1) / kScanTile;
+    const uint32_t acc_grid = std::min((o.cap_acc + kScanTile - 1) / kScanTile, max_blocks);
     e = device_scan<PairMaxOp, false>(o.runs, o.runs, o.n_acc, 0, acc_grid, o.scan_tot, 0, s);
     if (e != cudaSuccess) return joined(e);
     k_ord_acc<<<stream_blocks, 256, 0, s>>>(o);
