@@ -689,7 +689,7 @@ int hetm_init(hetm_ctx **out, uint64_t stmr_words, uint32_t granule_bytes, const
         if (o.key_bits == 0) o.key_bits = 1;
         const uint64_t hist_n = 256ull * ((o.cap_acc + 2047) / 2048);
         const uint64_t tot_n = std::max<uint64_t>(hist_n, o.cap_acc) / 1024 + 2;
-        if (!dev_alloc_t(c, &o.cnt, o.cap_tx) || !dev_alloc_t(c, &o.scan_tot, tot_n) ||
+        if (!dev_alloc_t(c, &o.scan_tot, tot_n) ||
             !dev_alloc_t(c, &o.keys0, o.cap_acc) || !dev_alloc_t(c, &o.vals0, o.cap_acc) ||
             !dev_alloc_t(c, &o.keys1, o.cap_acc) || !dev_alloc_t(c, &o.vals1, o.cap_acc) ||
             !dev_alloc_t(c, &o.hist, hist_n) || !dev_alloc_t(c, &o.runs, o.cap_acc) ||

@@ -130,8 +130,7 @@ static_assert(sizeof(OrdRec) == 80, "80-byte record");
 // Scratch of the ordered executor (capacities fixed at context creation).
 struct OrderArgs {
     ExecArgs e;
-    uint64_t *cnt;              // [cap_tx] per-tx (1 << 32 | #resources) -> exclusive prefix
-    uint64_t *scan_tot;         // per-tile totals of the scans
+    uint64_t *scan_tot;         // per-tile totals of the scans (and of the ranking)
     uint32_t *keys0, *vals0;    // [cap_acc] access list, sorted in place
     uint32_t *keys1, *vals1;    // [cap_acc] radix-sort ping-pong buffers
     uint64_t *hist;             // [256 * ceil(cap_acc / 2048)] digit counts

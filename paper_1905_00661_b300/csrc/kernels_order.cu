@@ -390,12 +390,24 @@ __device__ __forceinline__ bool view_tx(const ExecArgs &a, uint64_t u, TxView &t
     return false;
 }
 
-__global__ void __launch_bounds__(256) k_ord_count(OrderArgs o) {
+// Ranks of the ordered phase.  The serial order is the launch order, so a
+// transaction's rank and the offset of its accesses are the exclusive
+// prefix, over the launch, of (1 << 32 | its resource count) for the
+// transactions the ordered phase runs.  k_ord_count sums that value over
+// each tile of kScanTile launch indices into scan_tot[tile]; the tile sums
+// are scanned in place (k_scan_totals); k_ord_emit works each value out
+// again and scans inside its tile.  Tiles are walked in rounds of 256
+// consecutive indices, one per thread, so that a warp's record loads are
+// contiguous.
+__device__ __forceinline__ uint64_t ord_value(bool ok, const TxView &t) {
+    return ok && t.n ? (1ull << 32) | t.n : 0ull;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_ord_count(OrderArgs o) {
+    __shared__ uint64_t s_warp[kScanThreads / 32];
     const ExecArgs &a = o.e;
     const uint64_t total = a.rp->total_tx;
-    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
-    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    if (tid == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         *o.n_tx32 = (uint32_t)total;
         *o.n_cache_runs = 0;
         const unsigned long long v0 = *a.gv;
@@ -404,27 +416,33 @@ __global__ void __launch_bounds__(256) k_ord_count(OrderArgs o) {
     }
     unsigned long long bad = 0;
     const unsigned lane = threadIdx.x & 31u;
-    // loop bound rounded up to whole warps: the W2 list is appended warp by warp
-    const uint64_t span = (total + 31) & ~31ull;
-    for (uint64_t u = tid; u < span; u += stride) {
-        TxView t;
-        bool ok = false, tail = false;
-        if (u < total) {
-            ok = view_tx(a, u, t);
-            o.cnt[u] = ok && t.n ? (1ull << 32) | t.n : 0ull;
-            if (!ok) {  // out-of-range words or unknown workload: not executed
-                if (t.d->status) t.d->status[t.li] = kGaveUp;
-                ++bad;
+    const uint64_t nt = (total + kScanTile - 1) / kScanTile;
+    for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        uint64_t sum = 0;
+        for (int r = 0; r < kScanItems; ++r) {
+            const uint64_t u = tile * kScanTile + (uint64_t)r * kScanThreads + threadIdx.x;
+            TxView t;
+            bool ok = false, tail = false;
+            if (u < total) {
+                ok = view_tx(a, u, t);
+                sum += ord_value(ok, t);
+                if (!ok) {  // out-of-range words or unknown workload: not executed
+                    if (t.d->status) t.d->status[t.li] = kGaveUp;
+                    ++bad;
+                }
+                tail = ok && t.tail;
             }
-            tail = ok && t.tail;
+            // the W2 updates are listed warp by warp
+            const unsigned m = __ballot_sync(kFull, tail);
+            if (m && o.w2list) {
+                unsigned long long base = 0;
+                if (lane == (unsigned)(__ffs(m) - 1)) base = atomicAdd(o.w2n, (unsigned long long)__popc(m));
+                base = __shfl_sync(kFull, base, __ffs(m) - 1);
+                if (tail) o.w2list[base + __popc(m & lanemask_lt())] = (uint32_t)u;
+            }
         }
-        const unsigned m = __ballot_sync(kFull, tail);
-        if (m && o.w2list) {
-            unsigned long long base = 0;
-            if (lane == (unsigned)(__ffs(m) - 1)) base = atomicAdd(o.w2n, (unsigned long long)__popc(m));
-            base = __shfl_sync(kFull, base, __ffs(m) - 1);
-            if (tail) o.w2list[base + __popc(m & lanemask_lt())] = (uint32_t)u;
-        }
+        const uint64_t incl = block_scan_incl(sum, SumOp(), s_warp);
+        if (threadIdx.x == kScanThreads - 1) o.scan_tot[tile] = incl;
     }
     if (bad) {
         set_err(a.err, kErrAddr);
@@ -433,32 +451,43 @@ __global__ void __launch_bounds__(256) k_ord_count(OrderArgs o) {
 }
 
 // access list entry: key = resource word, value = rank << 4 | slot << 2 | cache << 1 | writer
-__global__ void __launch_bounds__(256) k_ord_emit(OrderArgs o) {
+__global__ void __launch_bounds__(kScanThreads) k_ord_emit(OrderArgs o) {
+    __shared__ uint64_t s_warp[kScanThreads / 32];
     const ExecArgs &a = o.e;
     const uint64_t total = a.rp->total_tx;
-    const uint64_t stride = gridDim.x * (uint64_t)blockDim.x;
-    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < total; u += stride) {
-        TxView t;
-        const bool ok = view_tx(a, u, t);
-        const uint64_t c = o.cnt[u];  // exclusive prefix: (rank << 32) | offset
-        const uint32_t n = ok ? t.n : 0;
-        if (n) {
-            const uint32_t rank = (uint32_t)(c >> 32);
-            OrdRec &r = o.rec[rank];
-            r.u = (uint32_t)u;
-            r.meta = n | (t.wl << 3) | (t.map << 8) | (t.b << 16);
-            r.aux = t.aux;
-            r.li = t.li;
-            const uint32_t cache = t.wl == HETM_WL_CACHE ? 2u : 0u;
-            for (uint32_t k = 0; k < n; ++k) {
-                r.addr[k] = t.addr[k];
-                o.keys0[(uint32_t)c + k] = t.addr[k];
-                o.vals0[(uint32_t)c + k] = (rank << 4) | (k << 2) | cache | ((t.wmask >> k) & 1u);
+    const uint64_t nt = (total + kScanTile - 1) / kScanTile;
+    for (uint64_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+        uint64_t carry = o.scan_tot[tile];  // exclusive prefix of the tile
+        for (int r = 0; r < kScanItems; ++r) {
+            const uint64_t u = tile * kScanTile + (uint64_t)r * kScanThreads + threadIdx.x;
+            TxView t;
+            bool ok = false;
+            if (u < total) ok = view_tx(a, u, t);
+            const uint64_t v = u < total ? ord_value(ok, t) : 0ull;
+            const uint64_t incl = block_scan_incl(v, SumOp(), s_warp);
+            const uint64_t c = carry + incl - v;  // exclusive prefix: (rank << 32) | offset
+            carry += s_warp[kScanThreads / 32 - 1];  // the round's total
+            __syncthreads();  // s_warp is rewritten by the next round's scan
+            if (u >= total) continue;
+            const uint32_t n = ok ? t.n : 0;
+            if (n) {
+                const uint32_t rank = (uint32_t)(c >> 32);
+                OrdRec &rr = o.rec[rank];
+                rr.u = (uint32_t)u;
+                rr.meta = n | (t.wl << 3) | (t.map << 8) | (t.b << 16);
+                rr.aux = t.aux;
+                rr.li = t.li;
+                const uint32_t cache = t.wl == HETM_WL_CACHE ? 2u : 0u;
+                for (uint32_t k = 0; k < n; ++k) {
+                    rr.addr[k] = t.addr[k];
+                    o.keys0[(uint32_t)c + k] = t.addr[k];
+                    o.vals0[(uint32_t)c + k] = (rank << 4) | (k << 2) | cache | ((t.wmask >> k) & 1u);
+                }
             }
-        }
-        if (u == total - 1) {
-            *o.n_acc = (uint32_t)c + n;
-            *o.n_ord = (uint32_t)(c >> 32) + (n ? 1u : 0u);
+            if (u == total - 1) {
+                *o.n_acc = (uint32_t)c + n;
+                *o.n_ord = (uint32_t)(c >> 32) + (n ? 1u : 0u);
+            }
         }
     }
     if (total == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1441,7 +1470,7 @@ cudaError_t launch_ro_phase(const ExecArgs &e, unsigned long long *v0, int block
 
 cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_blocks,
                            cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
-    k_ord_count<<<stream_blocks, 256, 0, s>>>(o);
+    k_ord_count<<<stream_blocks, kScanThreads, 0, s>>>(o);
     // The read-only phase needs only the clock snapshot k_ord_count takes and
     // the launch-start STMR^W, which nothing changes before k_seg_exec: with a
     // side stream it runs beside the ordering pre-pass.
@@ -1465,10 +1494,9 @@ cudaError_t launch_ordered(const OrderArgs &o, int exec_blocks, int stream_block
         return err;
     };
     const uint32_t max_blocks = (uint32_t)std::max(stream_blocks, 1);
-    const uint32_t scan_grid = std::min((o.cap_tx + kScanTile - 1) / kScanTile, max_blocks);
-    cudaError_t e = device_scan<SumOp, true>(o.cnt, o.cnt, o.n_tx32, 0, scan_grid, o.scan_tot, 0, s);
-    if (e != cudaSuccess) return joined(e);
-    k_ord_emit<<<stream_blocks, 256, 0, s>>>(o);
+    k_scan_totals<SumOp><<<1, kScanThreads, 0, s>>>(o.scan_tot, o.n_tx32, 0, 0ull);
+    k_ord_emit<<<stream_blocks, kScanThreads, 0, s>>>(o);
+    cudaError_t e = cudaGetLastError();
     e = radix_sort(o.keys0, o.vals0, o.keys1, o.vals1, o.n_acc, o.cap_acc, o.key_bits, o.hist,
                    o.scan_tot, o.n_hist, max_blocks, s);
     if (e != cudaSuccess) return joined(e);
