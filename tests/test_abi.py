@@ -47,6 +47,22 @@ def test_strerror_and_defaults_without_gpu():
     assert cfg.exec_mode == h.HETM_EXEC_ORDERED and cfg.max_round_tx == 1 << 22
 
 
+def test_round_codes_the_binding_returns_as_stats():
+    """A round call returns its stats when the code is the device error the
+    round itself reports (a timeout, an address error, a CPU timestamp out of
+    range or repeated); any other code -- an argument error before the round
+    ran, a CUDA failure -- raises."""
+    import paper_1905_00661_b300 as h
+    ok = h._round_reported
+    assert ok(h.HETM_OK, {"err": h.HETM_OK})
+    for code in (h.HETM_ETIMEOUT, h.HETM_EDEVICE, h.HETM_EINVAL):
+        assert ok(code, {"err": code})
+        assert not ok(code, {"err": h.HETM_OK})
+    assert not ok(h.HETM_ECUDA, {"err": h.HETM_OK})
+    assert not ok(h.HETM_EBUSY, {"err": h.HETM_OK})
+    assert not ok(h.HETM_EINVAL, {"err": h.HETM_EDEVICE})
+
+
 def test_record_layouts_match_workloads():
     import paper_1905_00661_b300 as h
     import workloads as wl
