@@ -91,33 +91,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint64_t *in,
     Op op;
     // a grid of the machine's size walks the tiles the count fills
     for (uint32_t tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const uint64_t base = (uint64_t)tile * kScanTile;
-    uint64_t x[kScanItems];
-    uint64_t run = identity;
+        const uint64_t base = (uint64_t)tile * kScanTile;
+        uint64_t x[kScanItems];
+        uint64_t run = identity;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const uint64_t i = base + threadIdx.x * kScanItems + k;
-        x[k] = i < n ? in[i] : identity;
-        run = op(run, x[k]);
-    }
-    const uint64_t incl = block_scan_incl(run, op, s_warp);
-    uint64_t pre = __shfl_up_sync(kFull, incl, 1);
-    // exclusive prefix of this thread's items inside the tile
-    {
-        const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-        if (lane == 0) pre = warp == 0 ? identity : s_warp[warp - 1];
-        // s_warp was overwritten by the scan with inclusive warp totals
-    }
-    uint64_t acc = pre;
+        for (int k = 0; k < kScanItems; ++k) {
+            const uint64_t i = base + threadIdx.x * kScanItems + k;
+            x[k] = i < n ? in[i] : identity;
+            run = op(run, x[k]);
+        }
+        const uint64_t incl = block_scan_incl(run, op, s_warp);
+        uint64_t pre = __shfl_up_sync(kFull, incl, 1);
+        // exclusive prefix of this thread's items inside the tile
+        {
+            const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+            if (lane == 0) pre = warp == 0 ? identity : s_warp[warp - 1];
+            // s_warp was overwritten by the scan with inclusive warp totals
+        }
+        uint64_t acc = pre;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const uint64_t i = base + threadIdx.x * kScanItems + k;
-        const uint64_t nxt = op(acc, x[k]);
-        if (i < n) out[i] = kExclusive ? acc : nxt;
-        acc = nxt;
-    }
-    if (threadIdx.x == kScanThreads - 1) tot[tile] = incl;
-    __syncthreads();  // s_warp is refilled by the next tile's scan
+        for (int k = 0; k < kScanItems; ++k) {
+            const uint64_t i = base + threadIdx.x * kScanItems + k;
+            const uint64_t nxt = op(acc, x[k]);
+            if (i < n) out[i] = kExclusive ? acc : nxt;
+            acc = nxt;
+        }
+        if (threadIdx.x == kScanThreads - 1) tot[tile] = incl;
+        __syncthreads();  // s_warp is refilled by the next tile's scan
     }
 }
 
@@ -225,42 +225,42 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t *
     const uint32_t n_tiles = (n + kSortTile - 1) / kSortTile;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     for (uint32_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const uint64_t base = (uint64_t)tile * kSortTile;
-    s_base[threadIdx.x] = (uint32_t)hist_ex[(uint64_t)threadIdx.x * n_tiles + tile];
-    for (int r = 0; r < kSortItems; ++r) {
-        for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][threadIdx.x] = 0;
-        __syncthreads();
-        const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
-        const bool ok = i < n;
-        const uint32_t key = ok ? kin[i] : 0u;
-        const uint32_t val = ok ? vin[i] : 0u;
-        const uint32_t d = ok ? (key >> shift) & 255u : 256u + lane;  // padding: unique
-        const unsigned peers = __match_any_sync(kFull, d);
-        const uint32_t rank = __popc(peers & lanemask_lt());
-        if (ok && rank == 0) s_wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        // digit-wise exclusive prefix over the warps of this round
-        uint32_t run = 0;
-        {
-            const uint32_t dd = threadIdx.x;
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                const uint32_t c = s_wcnt[w][dd];
-                s_wcnt[w][dd] = run;
-                run += c;
+        const uint64_t base = (uint64_t)tile * kSortTile;
+        s_base[threadIdx.x] = (uint32_t)hist_ex[(uint64_t)threadIdx.x * n_tiles + tile];
+        for (int r = 0; r < kSortItems; ++r) {
+            for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][threadIdx.x] = 0;
+            __syncthreads();
+            const uint64_t i = base + (uint64_t)r * kSortThreads + threadIdx.x;
+            const bool ok = i < n;
+            const uint32_t key = ok ? kin[i] : 0u;
+            const uint32_t val = ok ? vin[i] : 0u;
+            const uint32_t d = ok ? (key >> shift) & 255u : 256u + lane;  // padding: unique
+            const unsigned peers = __match_any_sync(kFull, d);
+            const uint32_t rank = __popc(peers & lanemask_lt());
+            if (ok && rank == 0) s_wcnt[warp][d] = __popc(peers);
+            __syncthreads();
+            // digit-wise exclusive prefix over the warps of this round
+            uint32_t run = 0;
+            {
+                const uint32_t dd = threadIdx.x;
+                for (int w = 0; w < kSortThreads / 32; ++w) {
+                    const uint32_t c = s_wcnt[w][dd];
+                    s_wcnt[w][dd] = run;
+                    run += c;
+                }
             }
-        }
-        __syncthreads();
-        if (ok) {
-            const uint32_t pos = s_base[d] + s_wcnt[warp][d] + rank;
-            if (pos < n) {  // always true for a consistent histogram
-                kout[pos] = key;
-                vout[pos] = val;
+            __syncthreads();
+            if (ok) {
+                const uint32_t pos = s_base[d] + s_wcnt[warp][d] + rank;
+                if (pos < n) {  // always true for a consistent histogram
+                    kout[pos] = key;
+                    vout[pos] = val;
+                }
             }
+            __syncthreads();
+            s_base[threadIdx.x] += run;
+            __syncthreads();
         }
-        __syncthreads();
-        s_base[threadIdx.x] += run;
-        __syncthreads();
-    }
     }
 }
 
